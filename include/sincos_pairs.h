@@ -1,0 +1,249 @@
+/*
+ * sincos_pairs.h -- C ABI of the GB300 (sm_103a) sine-cosine pair library.
+ *
+ * The library computes single-precision sine-cosine pairs with the
+ * branch-free method of M. H. Mendenhall, "A Fast, Vectorizable Algorithm
+ * for Producing Single-Precision Sine-Cosine Pairs" (cs/0406049):
+ *   - the angle is scaled by 1/(2 pi) and reduced onto [-1/2, 1/2] by
+ *     rounding to nearest (ties to even) and subtracting (Sec. Methodology);
+ *   - power series in the reduced value give the sine and cosine of the
+ *     quarter angle (Sec. Methodology, the printed coefficient sets);
+ *   - two double-angle steps of Eq. (1), s' = 2 s c and c' = c^2 - s^2,
+ *     expand the pair to the full circle;
+ *   - the amplitude drift is corrected by a factor computed from the
+ *     half-angle pair (Sec. Methodology; Fig. 1).
+ * Everything runs in hand-written CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   Memory     All array arguments are caller-owned.  Unless an entry point
+ *              says otherwise they are device (or managed) memory of the
+ *              current CUDA device.  No entry point allocates per call,
+ *              except where stated (batched scratch, host-path streams).
+ *   Layout     Structure of arrays: one contiguous array of angles in, one of
+ *              sines and one of cosines out (the paper's `struct phase` holds
+ *              the two vectors separately).  Element i of every array belongs
+ *              to angle i.  Any 4-byte-aligned float pointer (2-byte for
+ *              16-bit outputs) is accepted; the kernels peel to 16-byte
+ *              alignment themselves.
+ *   Streams    Every call is asynchronous and ordered on `stream` (NULL is the
+ *              legacy default stream).  SINCOS_OK means "enqueued"; results
+ *              are valid once the stream has reached that point.
+ *   Errors     Invalid arguments are rejected on the host before anything is
+ *              enqueued: SINCOS_EINVAL (null pointer with n > 0, n < 0, bad
+ *              enum), SINCOS_EOVERLAP (outputs overlap each other, or the
+ *              input partially overlaps an output).  A failed CUDA call gives
+ *              SINCOS_ECUDA and its text is kept for sincos_last_error().
+ *              n == 0 (or count == 0) returns SINCOS_OK and enqueues nothing.
+ *   Threads    Calls on different streams may run concurrently from any
+ *              number of host threads.
+ *   Device     All calls act on the calling thread's current CUDA device.
+ */
+#ifndef SINCOS_PAIRS_H
+#define SINCOS_PAIRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so the header needs no CUDA headers. */
+struct CUstream_st;
+typedef struct CUstream_st *sincos_stream_t;
+
+typedef enum {
+    SINCOS_OK = 0,
+    SINCOS_EINVAL = -1,       /* bad argument (null pointer, negative size, bad enum) */
+    SINCOS_EOVERLAP = -2,     /* forbidden overlap between input and output arrays     */
+    SINCOS_ECUDA = -3,        /* a CUDA runtime call failed; see sincos_last_error()  */
+    SINCOS_EUNSUPPORTED = -4, /* the device is not an sm_103 GPU, or a size limit hit  */
+    SINCOS_ECAPTURE = -5      /* the call would allocate while its stream is captured  */
+} sincos_status;
+
+/* Output element type.  BF16 and F16 results are the binary32 result rounded
+ * to nearest, ties to even. */
+typedef enum { SINCOS_F32 = 0, SINCOS_BF16 = 1, SINCOS_F16 = 2 } sincos_dtype;
+
+/* Range reduction.
+ * PLAIN        -- the paper's: x1 = fl(x * K), K = fl(1/(2*3.1415926536)),
+ *                 q = x1 - rint(x1) (Sec. Methodology; Fig. 1).  The rounding
+ *                 of x*K costs about 2 pi |x1| 2^-24 of angle for large |x|.
+ * COMPENSATED  -- not in the paper: 1/(2 pi) split as Khi + Klo,
+ *                 r = rint(fl(x*Khi)); q = fma(x, Khi, -r); q = fma(x, Klo, q);
+ *                 q -= rint(q).  Within 7e-7 of FP64 for |x| <= 1e5. */
+typedef enum { SINCOS_RED_PLAIN = 0, SINCOS_RED_COMPENSATED = 1 } sincos_reduction;
+
+/* Series coefficients.
+ * NORMALIZED -- the first method's least-squares sine/cosine series with the
+ *               2 - s^2 - c^2 drift factor (Sec. Methodology, first method).
+ * DAGGER     -- the second method's un-normalized series (fit to the angle)
+ *               with the exact reciprocal 1/(s^2 + c^2) (Sec. Methodology,
+ *               second method). */
+typedef enum { SINCOS_COEF_NORMALIZED = 0, SINCOS_COEF_DAGGER = 1 } sincos_coef;
+
+/* ------------------------------------------------------------------------ */
+/* Forward                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* s[i], c[i] = sin(x[i]), cos(x[i]) for 0 <= i < n: binary32 in, binary32
+ * out, plain reduction, normalized coefficients -- the method exactly as the
+ * paper gives it (Sec. Methodology; Fig. 1).
+ *   x  device, n floats, read only.  May be the same pointer as s or c (in
+ *      place); any other overlap with s or c is SINCOS_EOVERLAP.
+ *   s  device, n floats, written.  c  device, n floats, written.
+ *      s and c must not overlap.
+ * NaN or +-Inf angles give NaN; |fl(x*K)| >= 2^23 gives (0, 1). */
+int sincos_pairs(const float *x, float *s, float *c, int64_t n, sincos_stream_t stream);
+
+/* General forward: output dtype, reduction and coefficient set chosen by the
+ * caller (Sec. Methodology; first and second methods).  s and c point to n
+ * elements of `out_dtype` (4 or 2 bytes each).  In-place (x == s or x == c)
+ * is allowed only for SINCOS_F32. */
+int sincos_pairs_ex(const float *x, void *s, void *c, int64_t n, int out_dtype,
+                    int reduction, int coef, sincos_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Backward                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Gradient of L = sum(gs*sin(x) + gc*cos(x)) with respect to x, evaluated on
+ * the forward's outputs: gx[i] = fma(gs[i], c[i], -(gc[i]*s[i])).  The method
+ * has no seams inside (-pi, pi) (Sec. Methodology), so the analytic
+ * derivative of the pair is the pair itself.
+ *   gs, gc  device, n floats, read only; either may be NULL for an all-zero
+ *           upstream gradient (gs == NULL: gx = -(gc*s); gc == NULL:
+ *           gx = gs*c; both NULL: gx = +0).
+ *   s, c    device, n floats: the forward's binary32 outputs, read only.
+ *   gx      device, n floats, written; may be the same pointer as one of the
+ *           inputs, no other overlap allowed. */
+int sincos_backward(const float *gs, const float *gc, const float *s, const float *c,
+                    float *gx, int64_t n, sincos_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched: many arrays of uneven length in one persistent launch            */
+/* ------------------------------------------------------------------------ */
+
+/* One array of the batch: x has lens[i] floats; s and c have lens[i]
+ * elements of the batch's output dtype.  All three are device pointers. */
+typedef struct {
+    const float *x;
+    void *s;
+    void *c;
+} sincos_seg;
+
+/* The forward over `count` independent arrays in one launch pair (a tiny
+ * prefix-sum kernel over the lengths, then one persistent kernel whose CTAs
+ * each take a contiguous run of fixed-size tiles of the concatenated element
+ * space).  Same per-element arithmetic as sincos_pairs_ex.
+ *   segs  device array of `count` descriptors, read by the kernels.
+ *   lens  device array of `count` int64 lengths; a negative length counts
+ *         as 0.  Both arrays are read when the kernels run, so they may be
+ *         filled by earlier work on the same stream.
+ * Outputs of different segments must not overlap (not checked: the
+ * descriptors live on the device).
+ * Scratch: the library keeps one small device buffer ((count+1) int64) per
+ * (device, stream) pair, allocated with cudaMalloc on the first call that
+ * needs a larger one.  A call that would allocate while `stream` is being
+ * captured returns SINCOS_ECAPTURE; make one uncaptured call first.
+ * sincos_batched_release() frees all such buffers (call it only when no
+ * batched work is in flight). */
+int sincos_batched(const sincos_seg *segs, const int64_t *lens, int count,
+                   sincos_stream_t stream);
+int sincos_batched_ex(const sincos_seg *segs, const int64_t *lens, int count, int out_dtype,
+                      int reduction, int coef, sincos_stream_t stream);
+int sincos_batched_release(void);
+
+/* A batched launch captured once into a CUDA graph and replayed.  The graph
+ * owns its scratch; the segs/lens device arrays are read at every replay,
+ * so their contents (not their addresses) may change between replays. */
+typedef struct sincos_graph_s *sincos_graph;
+int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int count,
+                                int out_dtype, int reduction, int coef, sincos_graph *out);
+int sincos_batched_graph_launch(sincos_graph g, sincos_stream_t stream);
+int sincos_batched_graph_destroy(sincos_graph g);
+
+/* ------------------------------------------------------------------------ */
+/* Host buffers: chunked, pipelined host -> device -> host                   */
+/* ------------------------------------------------------------------------ */
+
+/* The forward on host arrays.  x_host (n floats) is copied to the device in
+ * chunks, each chunk is computed, and s_host / c_host (n elements of
+ * out_dtype) are copied back, with copies and kernels of different chunks
+ * overlapped on internal streams.  Page-locked host memory gives full
+ * overlap; pageable memory works but the copies are staged by the driver.
+ *   dev_ws   caller-owned device workspace of ws_bytes, used as three
+ *            rotating chunk buffers; sincos_host_workspace_bytes() gives the
+ *            size for a given chunk length.  Must be 256-byte aligned.
+ * The call is ordered after earlier work on `stream`, and later work on
+ * `stream` waits for all its copies.  Host buffers must stay valid until
+ * then.  The library creates its internal streams and events once per
+ * device, on first use. */
+int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n,
+                      int out_dtype, int reduction, int coef, void *dev_ws, size_t ws_bytes,
+                      sincos_stream_t stream);
+size_t sincos_host_workspace_bytes(int out_dtype, int64_t chunk_elems);
+
+/* ------------------------------------------------------------------------ */
+/* Launch plans and the autotuner                                            */
+/* ------------------------------------------------------------------------ */
+
+typedef enum { SINCOS_OP_PAIRS = 0, SINCOS_OP_BACKWARD = 1, SINCOS_OP_BATCHED = 2 } sincos_op;
+
+/* A launch configuration: threads per CTA, vectors each thread keeps in
+ * flight per iteration (16-byte loads), and resident CTAs per SM that the
+ * grid is sized for.  A batched tile is block * unroll * vector-width
+ * elements. */
+typedef struct {
+    int block;        /* 64 .. 1024, multiple of 32 */
+    int unroll;       /* 1, 2, 4 or 8 */
+    int ctas_per_sm;  /* 1 .. 32 */
+    int reserved;     /* 0 */
+} sincos_plan;
+
+/* The plan used for (op, out_dtype, n) on the current device: the tuned one
+ * if the cache holds it for n's power-of-two bucket, else the default.  For
+ * SINCOS_OP_BATCHED, n is the segment count. */
+int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan);
+/* Store a plan for (op, out_dtype, n's bucket) on the current device. */
+int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan);
+
+/* Time every candidate plan on the caller's own buffers (writes s and c; x
+ * must not alias them), store the fastest for this (op, dtype, n bucket) and
+ * return it in *best.  Synchronizes `stream`.  Must not be called while
+ * `stream` is captured. */
+int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_dtype,
+                          int reduction, int coef, sincos_stream_t stream, sincos_plan *best);
+int sincos_autotune_backward(const float *gs, const float *gc, const float *s, const float *c,
+                             float *gx, int64_t n, sincos_stream_t stream, sincos_plan *best);
+/* Same for the batched launch, timed on the caller's batch (outputs are
+ * written); the plan is stored under (SINCOS_OP_BATCHED, out_dtype, bucket
+ * of `count`), which is also the key batched calls look up. */
+int sincos_autotune_batched(const sincos_seg *segs, const int64_t *lens, int count,
+                            int out_dtype, int reduction, int coef, sincos_stream_t stream,
+                            sincos_plan *best);
+
+/* Plan cache as a small JSON file, keyed by device name and SM count.
+ * If the environment variable SINCOS_TUNE_CACHE names a file, it is loaded
+ * on first use. */
+int sincos_plan_cache_save(const char *path);
+int sincos_plan_cache_load(const char *path);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+const char *sincos_strerror(int status);
+/* Text of the last failed CUDA call on this host thread ("" if none). */
+const char *sincos_last_error(void);
+/* Kernel launches this library has enqueued since load (all threads); a
+ * graph replay counts the kernels in the graph. */
+uint64_t sincos_launch_count(void);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int sincos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SINCOS_PAIRS_H */

@@ -1,0 +1,305 @@
+"""Python binding of the C ABI, with the same names, plus the torch front end.
+
+The functions here only marshal arguments (device pointers, sizes, the
+current CUDA stream) into ``libsincos_gb300.so``; every step of the method
+runs in its CUDA kernels.  PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+_DTYPES = {torch.float32: _lib.F32, torch.bfloat16: _lib.BF16, torch.float16: _lib.F16}
+_DTYPE_NAMES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+_REDUCTIONS = {"plain": _lib.RED_PLAIN, "compensated": _lib.RED_COMPENSATED}
+_COEFS = {"normalized": _lib.COEF_NORMALIZED, "dagger": _lib.COEF_DAGGER}
+_OPS = {"pairs": _lib.OP_PAIRS, "backward": _lib.OP_BACKWARD, "batched": _lib.OP_BATCHED}
+
+
+def lib():
+    return _lib.load()
+
+
+def _torch_dtype(d) -> torch.dtype:
+    return _DTYPE_NAMES[d] if isinstance(d, str) else d
+
+
+def _stream(stream, device) -> int:
+    if stream is None:
+        return torch.cuda.current_stream(device).cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev(t: torch.Tensor, name: str, dtype=None) -> int:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _host(t: torch.Tensor, name: str, dtype=None) -> int:
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+# -----------------------------------------------------------------------------
+# C ABI, one function each
+# -----------------------------------------------------------------------------
+
+def sincos_pairs(x: torch.Tensor, s: torch.Tensor, c: torch.Tensor, stream=None) -> None:
+    """s, c = sin(x), cos(x): binary32, plain reduction, normalized set."""
+    n = x.numel()
+    if s.numel() != n or c.numel() != n:
+        raise ValueError("x, s and c must have the same number of elements")
+    with torch.cuda.device(x.device):
+        check(lib().sincos_pairs(_dev(x, "x", torch.float32), _dev(s, "s", torch.float32),
+                                 _dev(c, "c", torch.float32), n, _stream(stream, x.device)),
+              "sincos_pairs")
+
+
+def sincos_pairs_ex(x: torch.Tensor, s: torch.Tensor, c: torch.Tensor, reduction: str = "plain",
+                    coef: str = "normalized", stream=None) -> None:
+    """General forward; the output dtype is that of s and c (f32, bf16 or f16)."""
+    n = x.numel()
+    if s.numel() != n or c.numel() != n or s.dtype != c.dtype:
+        raise ValueError("s and c must match x in size and each other in dtype")
+    with torch.cuda.device(x.device):
+        check(lib().sincos_pairs_ex(_dev(x, "x", torch.float32), _dev(s, "s"), _dev(c, "c"), n,
+                                    _DTYPES[s.dtype], _REDUCTIONS[reduction], _COEFS[coef],
+                                    _stream(stream, x.device)),
+              "sincos_pairs_ex")
+
+
+def sincos_backward(gs, gc, s: torch.Tensor, c: torch.Tensor, gx: torch.Tensor,
+                    stream=None) -> None:
+    """gx = gs*c - gc*s; gs or gc may be None (an all-zero upstream gradient)."""
+    n = gx.numel()
+    for t in (gs, gc, s, c):
+        if t is not None and t.numel() != n:
+            raise ValueError("all arrays must have the same number of elements")
+    with torch.cuda.device(gx.device):
+        check(lib().sincos_backward(
+            None if gs is None else _dev(gs, "gs", torch.float32),
+            None if gc is None else _dev(gc, "gc", torch.float32),
+            _dev(s, "s", torch.float32), _dev(c, "c", torch.float32),
+            _dev(gx, "gx", torch.float32), n, _stream(stream, gx.device)),
+            "sincos_backward")
+
+
+def segments(x: torch.Tensor, s: torch.Tensor, c: torch.Tensor, offsets, lens):
+    """Device descriptor and length arrays for segments packed in x, s, c.
+
+    Segment i is elements [offsets[i], offsets[i] + lens[i]) of each of the
+    three flat arrays.  Returns (segs, lens) device tensors for sincos_batched."""
+    offsets = np.asarray(offsets, dtype=np.int64)
+    lens_np = np.asarray(lens, dtype=np.int64)
+    osz = s.element_size()
+    desc = np.empty((offsets.size, 3), dtype=np.uint64)
+    desc[:, 0] = np.uint64(_dev(x, "x", torch.float32)) + (offsets * 4).astype(np.uint64)
+    desc[:, 1] = np.uint64(_dev(s, "s")) + (offsets * osz).astype(np.uint64)
+    desc[:, 2] = np.uint64(_dev(c, "c")) + (offsets * osz).astype(np.uint64)
+    segs_t = torch.from_numpy(desc.view(np.int64).reshape(-1)).to(x.device)
+    lens_t = torch.from_numpy(lens_np).to(x.device)
+    return segs_t, lens_t
+
+
+def segments_from_lists(xs, ss, cs):
+    """Device descriptor and length arrays for separate per-segment tensors."""
+    desc = np.array([[_dev(a, "x", torch.float32), _dev(b, "s"), _dev(d, "c")]
+                     for a, b, d in zip(xs, ss, cs)], dtype=np.uint64)
+    lens_np = np.array([a.numel() for a in xs], dtype=np.int64)
+    dev = xs[0].device
+    return (torch.from_numpy(desc.view(np.int64).reshape(-1)).to(dev),
+            torch.from_numpy(lens_np).to(dev))
+
+
+def sincos_batched(segs: torch.Tensor, lens: torch.Tensor, out_dtype="f32",
+                   reduction: str = "plain", coef: str = "normalized", stream=None) -> None:
+    """All segments in one prefix + persistent tile launch."""
+    count = lens.numel()
+    with torch.cuda.device(lens.device):
+        check(lib().sincos_batched_ex(_dev(segs, "segs"), _dev(lens, "lens", torch.int64), count,
+                                      _DTYPES[_torch_dtype(out_dtype)], _REDUCTIONS[reduction],
+                                      _COEFS[coef], _stream(stream, lens.device)),
+              "sincos_batched_ex")
+
+
+def sincos_batched_release() -> None:
+    check(lib().sincos_batched_release(), "sincos_batched_release")
+
+
+class BatchedGraph:
+    """sincos_batched_graph_*: the batched launch captured once, replayed by launch()."""
+
+    def __init__(self, segs: torch.Tensor, lens: torch.Tensor, out_dtype="f32",
+                 reduction: str = "plain", coef: str = "normalized"):
+        self._keep = (segs, lens)
+        self.device = lens.device
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().sincos_batched_graph_create(
+                _dev(segs, "segs"), _dev(lens, "lens", torch.int64), lens.numel(),
+                _DTYPES[_torch_dtype(out_dtype)], _REDUCTIONS[reduction], _COEFS[coef],
+                ctypes.byref(self._h)), "sincos_batched_graph_create")
+
+    def launch(self, stream=None) -> None:
+        with torch.cuda.device(self.device):
+            check(lib().sincos_batched_graph_launch(self._h, _stream(stream, self.device)),
+                  "sincos_batched_graph_launch")
+
+    def close(self) -> None:
+        if self._h:
+            check(lib().sincos_batched_graph_destroy(self._h), "sincos_batched_graph_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sincos_host_workspace_bytes(out_dtype, chunk_elems: int) -> int:
+    return int(lib().sincos_host_workspace_bytes(_DTYPES[_torch_dtype(out_dtype)], chunk_elems))
+
+
+def sincos_pairs_host(x_host: torch.Tensor, s_host: torch.Tensor, c_host: torch.Tensor,
+                      workspace: torch.Tensor, reduction: str = "plain",
+                      coef: str = "normalized", stream=None) -> None:
+    """Forward on host tensors through a caller-provided device workspace."""
+    n = x_host.numel()
+    if s_host.numel() != n or c_host.numel() != n or s_host.dtype != c_host.dtype:
+        raise ValueError("s_host and c_host must match x_host in size and each other in dtype")
+    ws = _dev(workspace, "workspace")
+    with torch.cuda.device(workspace.device):
+        check(lib().sincos_pairs_host(
+            _host(x_host, "x_host", torch.float32), _host(s_host, "s_host"),
+            _host(c_host, "c_host"), n, _DTYPES[s_host.dtype], _REDUCTIONS[reduction],
+            _COEFS[coef], ws, workspace.numel() * workspace.element_size(),
+            _stream(stream, workspace.device)), "sincos_pairs_host")
+
+
+# -----------------------------------------------------------------------------
+# Plans and the autotuner
+# -----------------------------------------------------------------------------
+
+def sincos_plan_get(op: str, out_dtype, n: int) -> dict:
+    p = _lib.sincos_plan()
+    check(lib().sincos_plan_get(_OPS[op], _DTYPES[_torch_dtype(out_dtype)], n, ctypes.byref(p)),
+          "sincos_plan_get")
+    return p.as_dict()
+
+
+def sincos_plan_set(op: str, out_dtype, n: int, block: int, unroll: int, ctas_per_sm: int):
+    p = _lib.sincos_plan(block, unroll, ctas_per_sm, 0)
+    check(lib().sincos_plan_set(_OPS[op], _DTYPES[_torch_dtype(out_dtype)], n, ctypes.byref(p)),
+          "sincos_plan_set")
+
+
+def sincos_autotune_pairs(x, s, c, reduction: str = "plain", coef: str = "normalized",
+                          stream=None) -> dict:
+    p = _lib.sincos_plan()
+    with torch.cuda.device(x.device):
+        check(lib().sincos_autotune_pairs(
+            _dev(x, "x", torch.float32), _dev(s, "s"), _dev(c, "c"), x.numel(),
+            _DTYPES[s.dtype], _REDUCTIONS[reduction], _COEFS[coef], _stream(stream, x.device),
+            ctypes.byref(p)), "sincos_autotune_pairs")
+    return p.as_dict()
+
+
+def sincos_autotune_backward(gs, gc, s, c, gx, stream=None) -> dict:
+    p = _lib.sincos_plan()
+    with torch.cuda.device(gx.device):
+        check(lib().sincos_autotune_backward(
+            None if gs is None else _dev(gs, "gs", torch.float32),
+            None if gc is None else _dev(gc, "gc", torch.float32),
+            _dev(s, "s", torch.float32), _dev(c, "c", torch.float32),
+            _dev(gx, "gx", torch.float32), gx.numel(), _stream(stream, gx.device),
+            ctypes.byref(p)), "sincos_autotune_backward")
+    return p.as_dict()
+
+
+def sincos_autotune_batched(segs, lens, out_dtype="f32", reduction: str = "plain",
+                            coef: str = "normalized", stream=None) -> dict:
+    p = _lib.sincos_plan()
+    with torch.cuda.device(lens.device):
+        check(lib().sincos_autotune_batched(
+            _dev(segs, "segs"), _dev(lens, "lens", torch.int64), lens.numel(),
+            _DTYPES[_torch_dtype(out_dtype)], _REDUCTIONS[reduction], _COEFS[coef],
+            _stream(stream, lens.device), ctypes.byref(p)), "sincos_autotune_batched")
+    return p.as_dict()
+
+
+def sincos_plan_cache_save(path: str) -> None:
+    check(lib().sincos_plan_cache_save(path.encode()), "sincos_plan_cache_save")
+
+
+def sincos_plan_cache_load(path: str) -> None:
+    check(lib().sincos_plan_cache_load(path.encode()), "sincos_plan_cache_load")
+
+
+def sincos_launch_count() -> int:
+    return int(lib().sincos_launch_count())
+
+
+def sincos_version() -> int:
+    return int(lib().sincos_version())
+
+
+# -----------------------------------------------------------------------------
+# Torch front end
+# -----------------------------------------------------------------------------
+
+def sincos(x: torch.Tensor, out_dtype=torch.float32, reduction: str = "plain",
+           coef: str = "normalized"):
+    """(sin x, cos x) as two new tensors shaped like x."""
+    out_dtype = _torch_dtype(out_dtype)
+    xc = x.contiguous()
+    s = torch.empty(x.shape, dtype=out_dtype, device=x.device)
+    c = torch.empty(x.shape, dtype=out_dtype, device=x.device)
+    sincos_pairs_ex(xc, s, c, reduction, coef)
+    return s, c
+
+
+class SinCosFn(torch.autograd.Function):
+    """(s, c) = (sin x, cos x) with the hand-written backward gx = gs*c - gc*s."""
+
+    @staticmethod
+    def forward(ctx, x, reduction="plain", coef="normalized"):
+        s, c = sincos(x, torch.float32, reduction, coef)
+        ctx.save_for_backward(s, c)
+        return s, c
+
+    @staticmethod
+    def backward(ctx, gs, gc):
+        s, c = ctx.saved_tensors
+        gs = None if gs is None else gs.contiguous()
+        gc = None if gc is None else gc.contiguous()
+        gx = torch.empty_like(s)
+        sincos_backward(gs, gc, s, c, gx)
+        return gx, None, None
+
+
+def sincos_autograd(x: torch.Tensor, reduction: str = "plain", coef: str = "normalized"):
+    return SinCosFn.apply(x, reduction, coef)

@@ -1,0 +1,180 @@
+// api.cu -- C ABI entry points for the single-array forward and backward,
+// argument validation, device facts, error reporting and launch counting.
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace sincos_gb300 {
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_dev_mu;
+DeviceInfo g_devices[kMaxDevices];
+bool g_dev_ready[kMaxDevices] = {false};
+
+std::mutex g_occ_mu;
+std::unordered_map<uint64_t, int> g_occ;   // (kernel, block, device) -> resident CTAs per SM
+
+bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes)
+{
+    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + abytes;
+    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + bbytes;
+    return a0 < b1 && b0 < a1;
+}
+
+}  // namespace
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return SINCOS_ECUDA;
+}
+
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int check_launch(const char *what)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    count_launches(1);
+    return SINCOS_OK;
+}
+
+int current_device(const DeviceInfo **info)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return SINCOS_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    DeviceInfo &d = g_devices[dev];
+    if (!g_dev_ready[dev]) {
+        cudaDeviceProp prop;
+        e = cudaGetDeviceProperties(&prop, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+        d.ordinal = dev;
+        d.sms = prop.multiProcessorCount;
+        d.major = prop.major;
+        d.minor = prop.minor;
+        d.max_threads_per_sm = prop.maxThreadsPerMultiProcessor;
+        snprintf(d.name, sizeof d.name, "%s", prop.name);
+        g_dev_ready[dev] = true;
+    }
+    // The library carries sm_103a code only.
+    if (d.major != 10 || d.minor != 3) {
+        g_last_error = std::string("device ") + d.name + " is sm_" + std::to_string(d.major) +
+                       std::to_string(d.minor) + "; this library is built for sm_103a only";
+        return SINCOS_EUNSUPPORTED;
+    }
+    *info = &d;
+    return SINCOS_OK;
+}
+
+int resident_ctas(const void *kernel, int block, int want)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t key = ((uint64_t)(uintptr_t)kernel << 16) ^ ((uint64_t)block << 6) ^ (uint64_t)dev;
+    int per_sm = -1;
+    {
+        std::lock_guard<std::mutex> lock(g_occ_mu);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) per_sm = it->second;
+    }
+    if (per_sm < 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 0;
+        }
+        std::lock_guard<std::mutex> lock(g_occ_mu);
+        g_occ[key] = per_sm;
+    }
+    return per_sm < want ? per_sm : want;
+}
+
+bool valid_dtype(int d) { return d == SINCOS_F32 || d == SINCOS_BF16 || d == SINCOS_F16; }
+bool valid_reduction(int r) { return r == SINCOS_RED_PLAIN || r == SINCOS_RED_COMPENSATED; }
+bool valid_coef(int c) { return c == SINCOS_COEF_NORMALIZED || c == SINCOS_COEF_DAGGER; }
+
+}  // namespace sincos_gb300
+
+using namespace sincos_gb300;
+
+extern "C" {
+
+int sincos_pairs_ex(const float *x, void *s, void *c, int64_t n, int out_dtype, int reduction,
+                    int coef, sincos_stream_t stream)
+{
+    if (n < 0 || !valid_dtype(out_dtype) || !valid_reduction(reduction) || !valid_coef(coef))
+        return SINCOS_EINVAL;
+    if (n == 0) return SINCOS_OK;
+    if (!x || !s || !c) return SINCOS_EINVAL;
+    const size_t osz = (size_t)dtype_size(out_dtype);
+    const size_t xb = (size_t)n * 4, ob = (size_t)n * osz;
+    if (ranges_overlap(s, ob, c, ob)) return SINCOS_EOVERLAP;
+    bool in_place = false;
+    for (const void *o : {(const void *)s, (const void *)c}) {
+        if (!ranges_overlap(x, xb, o, ob)) continue;
+        if (o == (const void *)x && out_dtype == SINCOS_F32) in_place = true;
+        else return SINCOS_EOVERLAP;
+    }
+    const DeviceInfo *dev = nullptr;
+    int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    const sincos_plan plan = plan_for(*dev, SINCOS_OP_PAIRS, out_dtype, n);
+    return launch_forward(x, s, c, n, out_dtype, reduction, coef, in_place, plan, *dev,
+                          (cudaStream_t)stream);
+}
+
+int sincos_pairs(const float *x, float *s, float *c, int64_t n, sincos_stream_t stream)
+{
+    return sincos_pairs_ex(x, s, c, n, SINCOS_F32, SINCOS_RED_PLAIN, SINCOS_COEF_NORMALIZED, stream);
+}
+
+int sincos_backward(const float *gs, const float *gc, const float *s, const float *c, float *gx,
+                    int64_t n, sincos_stream_t stream)
+{
+    if (n < 0) return SINCOS_EINVAL;
+    if (n == 0) return SINCOS_OK;
+    if (!gx || ((gs || gc) && (!s || !c))) return SINCOS_EINVAL;
+    const size_t b = (size_t)n * 4;
+    bool in_place = false;
+    for (const float *in : {gs, gc, gs ? c : nullptr, gc ? s : nullptr}) {
+        if (!in || !ranges_overlap(in, b, gx, b)) continue;
+        if (in == gx) in_place = true;
+        else return SINCOS_EOVERLAP;
+    }
+    const DeviceInfo *dev = nullptr;
+    int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    const sincos_plan plan = plan_for(*dev, SINCOS_OP_BACKWARD, SINCOS_F32, n);
+    return launch_backward(gs, gc, s, c, gx, n, in_place, plan, *dev, (cudaStream_t)stream);
+}
+
+const char *sincos_strerror(int status)
+{
+    switch (status) {
+    case SINCOS_OK: return "ok";
+    case SINCOS_EINVAL: return "invalid argument";
+    case SINCOS_EOVERLAP: return "input and output arrays overlap in a way that is not allowed";
+    case SINCOS_ECUDA: return "a CUDA runtime call failed (see sincos_last_error)";
+    case SINCOS_EUNSUPPORTED: return "unsupported device or configuration";
+    case SINCOS_ECAPTURE: return "the call would allocate while its stream is being captured";
+    default: return "unknown status";
+    }
+}
+
+const char *sincos_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t sincos_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int sincos_version(void) { return 10000; }
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// internal.h -- host-side declarations shared by the library's translation
+// units.  Not part of the public ABI (that is include/sincos_pairs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sincos_pairs.h"
+
+namespace sincos_gb300 {
+
+// Cached facts about one CUDA device.
+struct DeviceInfo {
+    int ordinal = -1;
+    int sms = 0;
+    int major = 0, minor = 0;
+    int max_threads_per_sm = 0;
+    char name[256] = {0};
+};
+
+// The calling thread's current device (cached per ordinal).  Returns
+// SINCOS_OK and sets *info, or an error status (unsupported GPU, CUDA error).
+int current_device(const DeviceInfo **info);
+
+// Record a failed CUDA call for sincos_last_error(); returns SINCOS_ECUDA.
+int cuda_fail(cudaError_t e, const char *what);
+// cudaGetLastError() after a launch, mapped to a status.
+int check_launch(const char *what);
+// Count `k` kernel launches (sincos_launch_count()).
+void count_launches(uint64_t k);
+
+// Resident CTAs per SM of `kernel` at `block` threads (cached), capped by the
+// plan's request; at least 1 when the kernel fits at all, 0 when it does not.
+int resident_ctas(const void *kernel, int block, int want);
+
+bool valid_dtype(int d);
+bool valid_reduction(int r);
+bool valid_coef(int c);
+inline int dtype_size(int d) { return d == SINCOS_F32 ? 4 : 2; }
+
+// Plan lookup (tuned or default) for the current device.
+sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n);
+bool plan_valid(const sincos_plan &p);
+
+// Kernel launchers.  Arguments are already validated; they enqueue on `st`
+// and return a status.
+int launch_forward(const float *x, void *s, void *c, int64_t n, int dtype, int red, int coef,
+                   bool in_place, const sincos_plan &plan, const DeviceInfo &dev,
+                   cudaStream_t st);
+int launch_backward(const float *gs, const float *gc, const float *s, const float *c, float *gx,
+                    int64_t n, bool in_place, const sincos_plan &plan, const DeviceInfo &dev,
+                    cudaStream_t st);
+// Batched: prefix kernel over lens into `prefix` ((count+1) int64 of device
+// scratch), then the persistent tile kernel.
+int launch_batched(const sincos_seg *segs, const int64_t *lens, int count, int dtype, int red,
+                   int coef, int64_t *prefix, const sincos_plan &plan, const DeviceInfo &dev,
+                   cudaStream_t st);
+
+// Elements per batched tile for a plan and output dtype.
+int64_t batched_tile_elems(const sincos_plan &plan, int dtype);
+
+}  // namespace sincos_gb300

@@ -1,0 +1,370 @@
+// plans.cu -- launch plans: defaults, the tuned-plan cache (in memory and as
+// a JSON file) and the autotuner that fills it.
+//
+// A plan is (threads per CTA, 16-byte vectors in flight per thread, resident
+// CTAs per SM).  Plans are keyed by device ("<name>:<SMs>"), operation,
+// output dtype and the bit length of the element count, so one tuning run
+// per size class covers every later call in that class.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace sincos_gb300 {
+
+namespace {
+
+using PlanKey = std::tuple<std::string, int, int, int>;   // device, op, dtype, bucket
+
+std::mutex g_plan_mu;
+std::map<PlanKey, sincos_plan> g_plans;
+std::once_flag g_env_once;
+
+int bucket_of(int64_t n)
+{
+    int b = 0;
+    while (n > 0) {
+        ++b;
+        n >>= 1;
+    }
+    return b;
+}
+
+std::string device_key(const DeviceInfo &dev)
+{
+    return std::string(dev.name) + ":" + std::to_string(dev.sms);
+}
+
+sincos_plan default_plan(int op, int dtype)
+{
+    // 2048 resident threads per SM with several 16-byte loads each keeps
+    // enough bytes in flight to cover HBM latency on every SM.
+    if (op == SINCOS_OP_BACKWARD) return sincos_plan{256, 2, 8, 0};
+    if (dtype == SINCOS_F32) return sincos_plan{256, 4, 8, 0};
+    return sincos_plan{256, 2, 8, 0};
+}
+
+int load_file(const char *path);
+
+void load_env_cache()
+{
+    const char *p = std::getenv("SINCOS_TUNE_CACHE");
+    if (p && *p) load_file(p);
+}
+
+// Minimal reader for the file written by sincos_plan_cache_save: finds each
+// {...} object after "plans" and reads its string and integer fields.
+bool read_string(const char *&p, std::string &out)
+{
+    if (*p != '"') return false;
+    ++p;
+    out.clear();
+    while (*p && *p != '"') {
+        if (*p == '\\' && p[1]) ++p;
+        out.push_back(*p++);
+    }
+    if (*p != '"') return false;
+    ++p;
+    return true;
+}
+
+void skip_ws(const char *&p)
+{
+    while (*p == ' ' || *p == '\n' || *p == '\r' || *p == '\t' || *p == ',') ++p;
+}
+
+int load_file(const char *path)
+{
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return SINCOS_EINVAL;
+    std::string text;
+    char buf[4096];
+    size_t k;
+    while ((k = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, k);
+    std::fclose(f);
+    const char *p = std::strstr(text.c_str(), "\"plans\"");
+    if (!p) return SINCOS_EINVAL;
+    p = std::strchr(p, '[');
+    if (!p) return SINCOS_EINVAL;
+    ++p;
+    std::map<PlanKey, sincos_plan> loaded;
+    for (;;) {
+        skip_ws(p);
+        if (*p != '{') break;
+        ++p;
+        std::string device;
+        long op = -1, dtype = -1, bucket = -1, block = 0, unroll = 0, ctas = 0;
+        for (;;) {
+            skip_ws(p);
+            if (*p == '}') {
+                ++p;
+                break;
+            }
+            std::string key;
+            if (!read_string(p, key)) return SINCOS_EINVAL;
+            skip_ws(p);
+            if (*p != ':') return SINCOS_EINVAL;
+            ++p;
+            skip_ws(p);
+            if (*p == '"') {
+                std::string val;
+                if (!read_string(p, val)) return SINCOS_EINVAL;
+                if (key == "device") device = val;
+            } else {
+                char *end = nullptr;
+                const long v = std::strtol(p, &end, 10);
+                if (end == p) return SINCOS_EINVAL;
+                p = end;
+                if (key == "op") op = v;
+                else if (key == "dtype") dtype = v;
+                else if (key == "bucket") bucket = v;
+                else if (key == "block") block = v;
+                else if (key == "unroll") unroll = v;
+                else if (key == "ctas_per_sm") ctas = v;
+            }
+        }
+        sincos_plan plan{(int)block, (int)unroll, (int)ctas, 0};
+        if (device.empty() || op < 0 || dtype < 0 || bucket < 0 || !plan_valid(plan))
+            return SINCOS_EINVAL;
+        loaded[PlanKey(device, (int)op, (int)dtype, (int)bucket)] = plan;
+    }
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (auto &kv : loaded) g_plans[kv.first] = kv.second;
+    return SINCOS_OK;
+}
+
+void store_plan(const DeviceInfo &dev, int op, int dtype, int64_t n, const sincos_plan &p)
+{
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    g_plans[PlanKey(device_key(dev), op, dtype, bucket_of(n))] = p;
+}
+
+std::vector<sincos_plan> candidates(const DeviceInfo &dev)
+{
+    std::vector<sincos_plan> out;
+    const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
+    for (int block : {128, 256, 512, 1024})
+        for (int unroll : {1, 2, 4, 8})
+            for (int ctas : {1, 2, 4, 8, 16})
+                if (block * ctas <= max_threads) out.push_back(sincos_plan{block, unroll, ctas, 0});
+    return out;
+}
+
+// Median of `reps` timed runs of `launch` on `st` (after one warm-up run), in
+// milliseconds; a negative value if any launch fails.
+template <class F>
+float time_plan(F &&launch, cudaStream_t st, int reps)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    std::vector<float> ms;
+    bool ok = launch() == SINCOS_OK;
+    for (int r = 0; ok && r < reps; ++r) {
+        cudaEventRecord(a, st);
+        ok = launch() == SINCOS_OK;
+        cudaEventRecord(b, st);
+        if (ok && cudaEventSynchronize(b) == cudaSuccess) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, a, b);
+            ms.push_back(t);
+        } else {
+            ok = false;
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (!ok || ms.empty()) return -1.f;
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+}
+
+bool stream_is_capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+template <class F>
+int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F &&launch_with,
+         sincos_plan *best)
+{
+    if (stream_is_capturing(st)) return SINCOS_ECAPTURE;
+    float best_ms = -1.f;
+    sincos_plan best_plan = default_plan(op, dtype);
+    for (const sincos_plan &p : candidates(dev)) {
+        const float ms = time_plan([&] { return launch_with(p); }, st, 3);
+        if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best_plan = p;
+        }
+    }
+    if (best_ms < 0.f) return SINCOS_ECUDA;
+    store_plan(dev, op, dtype, n, best_plan);
+    if (best) *best = best_plan;
+    return SINCOS_OK;
+}
+
+}  // namespace
+
+bool plan_valid(const sincos_plan &p)
+{
+    return p.block >= 64 && p.block <= 1024 && p.block % 32 == 0 &&
+           (p.unroll == 1 || p.unroll == 2 || p.unroll == 4 || p.unroll == 8) &&
+           p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32;
+}
+
+sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n)
+{
+    std::call_once(g_env_once, load_env_cache);
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    auto it = g_plans.find(PlanKey(device_key(dev), op, dtype, bucket_of(n)));
+    return it != g_plans.end() ? it->second : default_plan(op, dtype);
+}
+
+// Defined in batched_api.cu: per-(device, stream) prefix scratch.
+int batched_scratch(cudaStream_t st, int count, int64_t **prefix);
+
+}  // namespace sincos_gb300
+
+using namespace sincos_gb300;
+
+extern "C" {
+
+int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan)
+{
+    if (!plan || op < 0 || op > 2 || !valid_dtype(out_dtype) || n < 0) return SINCOS_EINVAL;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    *plan = plan_for(*dev, op, out_dtype, n);
+    return SINCOS_OK;
+}
+
+int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan)
+{
+    if (!plan || op < 0 || op > 2 || !valid_dtype(out_dtype) || n < 0 || !plan_valid(*plan))
+        return SINCOS_EINVAL;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    std::call_once(g_env_once, load_env_cache);
+    store_plan(*dev, op, out_dtype, n, *plan);
+    return SINCOS_OK;
+}
+
+int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_dtype,
+                          int reduction, int coef, sincos_stream_t stream, sincos_plan *best)
+{
+    if (n <= 0 || !x || !s || !c || !valid_dtype(out_dtype) || !valid_reduction(reduction) ||
+        !valid_coef(coef))
+        return SINCOS_EINVAL;
+    const size_t xb = (size_t)n * 4, ob = (size_t)n * dtype_size(out_dtype);
+    const uintptr_t x0 = (uintptr_t)x;
+    for (const void *o : {(const void *)s, (const void *)c})
+        if (x0 < (uintptr_t)o + ob && (uintptr_t)o < x0 + xb) return SINCOS_EOVERLAP;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    std::call_once(g_env_once, load_env_cache);
+    cudaStream_t st = (cudaStream_t)stream;
+    return tune(*dev, SINCOS_OP_PAIRS, out_dtype, n, st,
+                [&](const sincos_plan &p) {
+                    return launch_forward(x, s, c, n, out_dtype, reduction, coef, false, p, *dev, st);
+                },
+                best);
+}
+
+int sincos_autotune_backward(const float *gs, const float *gc, const float *s, const float *c,
+                             float *gx, int64_t n, sincos_stream_t stream, sincos_plan *best)
+{
+    if (n <= 0 || !gx || !s || !c) return SINCOS_EINVAL;
+    for (const float *in : {gs, gc, s, c})
+        if (in && (uintptr_t)in < (uintptr_t)(gx + n) && (uintptr_t)gx < (uintptr_t)(in + n))
+            return SINCOS_EOVERLAP;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    std::call_once(g_env_once, load_env_cache);
+    cudaStream_t st = (cudaStream_t)stream;
+    return tune(*dev, SINCOS_OP_BACKWARD, SINCOS_F32, n, st,
+                [&](const sincos_plan &p) {
+                    return launch_backward(gs, gc, s, c, gx, n, false, p, *dev, st);
+                },
+                best);
+}
+
+int sincos_autotune_batched(const sincos_seg *segs, const int64_t *lens, int count,
+                            int out_dtype, int reduction, int coef, sincos_stream_t stream,
+                            sincos_plan *best)
+{
+    if (count <= 0 || !segs || !lens || !valid_dtype(out_dtype) || !valid_reduction(reduction) ||
+        !valid_coef(coef))
+        return SINCOS_EINVAL;
+    const DeviceInfo *dev = nullptr;
+    int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    std::call_once(g_env_once, load_env_cache);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (stream_is_capturing(st)) return SINCOS_ECAPTURE;
+    int64_t *prefix = nullptr;
+    rc = batched_scratch(st, count, &prefix);
+    if (rc != SINCOS_OK) return rc;
+    return tune(*dev, SINCOS_OP_BATCHED, out_dtype, count, st,
+                [&](const sincos_plan &p) {
+                    return launch_batched(segs, lens, count, out_dtype, reduction, coef, prefix, p,
+                                          *dev, st);
+                },
+                best);
+}
+
+int sincos_plan_cache_save(const char *path)
+{
+    if (!path) return SINCOS_EINVAL;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return SINCOS_EINVAL;
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    std::fprintf(f, "{\"version\": 1, \"plans\": [");
+    bool first = true;
+    for (auto &kv : g_plans) {
+        std::string dev;
+        for (char ch : std::get<0>(kv.first)) {
+            if (ch == '"' || ch == '\\') dev.push_back('\\');
+            dev.push_back(ch);
+        }
+        std::fprintf(f,
+                     "%s\n  {\"device\": \"%s\", \"op\": %d, \"dtype\": %d, \"bucket\": %d, "
+                     "\"block\": %d, \"unroll\": %d, \"ctas_per_sm\": %d}",
+                     first ? "" : ",", dev.c_str(), std::get<1>(kv.first), std::get<2>(kv.first),
+                     std::get<3>(kv.first), kv.second.block, kv.second.unroll,
+                     kv.second.ctas_per_sm);
+        first = false;
+    }
+    std::fprintf(f, "\n]}\n");
+    return std::fclose(f) == 0 ? SINCOS_OK : SINCOS_EINVAL;
+}
+
+int sincos_plan_cache_load(const char *path)
+{
+    if (!path) return SINCOS_EINVAL;
+    std::call_once(g_env_once, load_env_cache);
+    return load_file(path);
+}
+
+}  // extern "C"

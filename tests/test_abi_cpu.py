@@ -1,0 +1,119 @@
+"""The C-ABI library without a GPU: it loads, exports every declared symbol,
+and rejects invalid arguments on the host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_cs_0406049_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sincos_pairs.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    with open(HEADER) as f:
+        text = f.read()
+    return re.findall(r"^[a-z_ 0-9]+\**\s*\*?(sincos_\w+)\(", text, flags=re.M)
+
+
+def test_header_declares_the_entry_points():
+    names = set(declared_functions())
+    for n in ("sincos_pairs", "sincos_batched", "sincos_backward", "sincos_pairs_ex",
+              "sincos_pairs_host", "sincos_strerror"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared but not exported"
+        assert name in _lib.SIGNATURES, f"{name} has no Python binding"
+
+
+def test_binding_declares_nothing_extra():
+    assert set(_lib.SIGNATURES) == set(declared_functions())
+
+
+def test_status_strings(lib):
+    for st in (0, -1, -2, -3, -4, -5):
+        assert lib.sincos_strerror(st)
+    assert lib.sincos_version() >= 10000
+
+
+# Fake device addresses: validation rejects these calls before touching CUDA.
+A = 0x7f0000000000
+
+
+@pytest.mark.parametrize("args,status", [
+    ((A, A + 4096, A + 8192, -1, 0, 0, 0, None), _lib.EINVAL),            # n < 0
+    ((None, A + 4096, A + 8192, 16, 0, 0, 0, None), _lib.EINVAL),         # null x
+    ((A, None, A + 8192, 16, 0, 0, 0, None), _lib.EINVAL),                # null s
+    ((A, A + 4096, A + 8192, 16, 3, 0, 0, None), _lib.EINVAL),            # bad dtype
+    ((A, A + 4096, A + 8192, 16, 0, 2, 0, None), _lib.EINVAL),            # bad reduction
+    ((A, A + 4096, A + 8192, 16, 0, 0, 2, None), _lib.EINVAL),            # bad coefficients
+    ((A, A + 4096, A + 4100, 16, 0, 0, 0, None), _lib.EOVERLAP),          # s, c overlap
+    ((A, A + 4, A + 8192, 16, 0, 0, 0, None), _lib.EOVERLAP),             # x partly in s
+    ((A, A, A + 8192, 16, 1, 0, 0, None), _lib.EOVERLAP),                 # in place, 16-bit out
+    ((A, A + 4096, A + 8192, 0, 0, 0, 0, None), _lib.OK),                 # n == 0
+    ((None, None, None, 0, 0, 0, 0, None), _lib.OK),                      # n == 0, nulls
+])
+def test_forward_validation(lib, args, status):
+    assert lib.sincos_pairs_ex(*args) == status
+
+
+def test_plain_forward_validation(lib):
+    assert lib.sincos_pairs(A, A + 4096, A + 8192, -5, None) == _lib.EINVAL
+    assert lib.sincos_pairs(A, A + 4096, A + 4096, 8, None) == _lib.EOVERLAP
+    assert lib.sincos_pairs(A, A + 4096, A + 8192, 0, None) == _lib.OK
+
+
+def test_backward_validation(lib):
+    assert lib.sincos_backward(A, A + 4096, A + 8192, A + 12288, A + 16384, -1, None) == _lib.EINVAL
+    assert lib.sincos_backward(A, A + 4096, A + 8192, A + 12288, None, 8, None) == _lib.EINVAL
+    assert lib.sincos_backward(A, A + 4096, None, A + 12288, A + 16384, 8, None) == _lib.EINVAL
+    # gx partially overlapping an input
+    assert lib.sincos_backward(A, A + 4096, A + 8192, A + 12288, A + 8, 8, None) == _lib.EOVERLAP
+    assert lib.sincos_backward(None, None, None, None, A, 0, None) == _lib.OK
+
+
+def test_batched_validation(lib):
+    assert lib.sincos_batched(A, A + 4096, -1, None) == _lib.EINVAL
+    assert lib.sincos_batched(None, A + 4096, 4, None) == _lib.EINVAL
+    assert lib.sincos_batched(A, None, 4, None) == _lib.EINVAL
+    assert lib.sincos_batched(None, None, 0, None) == _lib.OK
+    assert lib.sincos_batched_ex(A, A + 4096, 4, 7, 0, 0, None) == _lib.EINVAL
+    h = ctypes.c_void_p()
+    assert lib.sincos_batched_graph_create(A, A + 8, 0, 0, 0, 0, ctypes.byref(h)) == _lib.EINVAL
+    assert lib.sincos_batched_graph_launch(None, None) == _lib.EINVAL
+    assert lib.sincos_batched_graph_destroy(None) == _lib.EINVAL
+
+
+def test_host_path_validation(lib):
+    ws = A
+    assert lib.sincos_pairs_host(A, A + 4096, A + 8192, -1, 0, 0, 0, ws, 1 << 20, None) == _lib.EINVAL
+    assert lib.sincos_pairs_host(A, A + 4096, A + 8192, 8, 0, 0, 0, ws + 4, 1 << 20, None) == _lib.EINVAL
+    assert lib.sincos_pairs_host(A, A + 4096, A + 8192, 8, 0, 0, 0, ws, 64, None) == _lib.EINVAL
+    assert lib.sincos_pairs_host(A, A + 4096, A + 4100, 8, 0, 0, 0, ws, 1 << 20, None) == _lib.EOVERLAP
+    assert lib.sincos_host_workspace_bytes(0, 64) == 3 * 64 * 12
+    assert lib.sincos_host_workspace_bytes(1, 65) == 3 * 128 * 8
+    assert lib.sincos_host_workspace_bytes(5, 64) == 0
+
+
+def test_plan_validation(lib):
+    bad = _lib.sincos_plan(100, 4, 8, 0)       # block not a multiple of 32
+    assert lib.sincos_plan_set(0, 0, 1 << 20, ctypes.byref(bad)) == _lib.EINVAL
+    bad = _lib.sincos_plan(256, 3, 8, 0)       # unroll not 1/2/4/8
+    assert lib.sincos_plan_set(0, 0, 1 << 20, ctypes.byref(bad)) == _lib.EINVAL
+    good = _lib.sincos_plan(256, 4, 8, 0)
+    assert lib.sincos_plan_set(9, 0, 1 << 20, ctypes.byref(good)) == _lib.EINVAL
+    assert lib.sincos_plan_get(0, 0, 1 << 20, None) == _lib.EINVAL
+    assert lib.sincos_plan_cache_load(b"/nonexistent/path.json") == _lib.EINVAL

@@ -1,0 +1,143 @@
+"""Batched forward (one prefix + persistent launch, and its CUDA graph)
+against the oracle applied to each array."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import as_np, assert_16_parity, assert_f32_parity, mixed_angles
+from paper_cs_0406049_gb300 import api, workloads
+
+pytestmark = pytest.mark.gpu
+
+DT = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def packed(lens, dtype, seed=0):
+    """Segments packed back to back in one buffer (most start unaligned)."""
+    lens = np.asarray(lens, np.int64)
+    total = int(np.clip(lens, 0, None).sum())
+    x = mixed_angles(max(total, 1), seed)[:total]
+    offs = np.concatenate([[0], np.cumsum(np.clip(lens, 0, None))[:-1]]).astype(np.int64)
+    xt = torch.from_numpy(x).cuda() if total else torch.empty(0, device="cuda")
+    s = torch.full((max(total, 1),), 7.0, device="cuda").to(DT[dtype])[:total]
+    c = torch.full((max(total, 1),), 7.0, device="cuda").to(DT[dtype])[:total]
+    return x, xt, s, c, offs
+
+
+def check_all(x, s, c, dtype, red, coef, what):
+    want_s, want_c = oracle.sincos(x, reduction=red, coef=coef, out=dtype)
+    if dtype == "f32":
+        assert_f32_parity(as_np(s), want_s, what + " s")
+        assert_f32_parity(as_np(c), want_c, what + " c")
+    else:
+        assert_16_parity(as_np(s), want_s, dtype == "bf16", what + " s")
+        assert_16_parity(as_np(c), want_c, dtype == "bf16", what + " c")
+
+
+EDGE_LENS = [1, 0, 3, 4095, 4096, 4097, 8191, 2, 65536 + 17, 5, 0, 0, 1, 1 << 20, 31, 7, 8]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("red,coef", [("plain", "normalized"), ("compensated", "dagger")])
+def test_edge_lengths(cuda_lib, dtype, red, coef):
+    x, xt, s, c, offs = packed(EDGE_LENS, dtype, seed=1)
+    segs, lens = api.segments(xt, s, c, offs, EDGE_LENS)
+    api.sincos_batched(segs, lens, dtype, red, coef)
+    check_all(x, s, c, dtype, red, coef, f"batched {dtype}")
+
+
+def test_negative_and_empty_lengths(cuda_lib):
+    lens = [5, -3, 0, 9, -100, 1]
+    x, xt, s, c, offs = packed(lens, "f32", seed=2)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    api.sincos_batched(segs, lens_t)
+    check_all(x, s, c, "f32", "plain", "normalized", "negative lengths")
+
+
+def test_separate_tensors_mixed_alignment(cuda_lib):
+    """Segments as separate tensors whose x, s and c start at different
+    offsets modulo 16 bytes (the element-wise path inside tiles)."""
+    rng = np.random.default_rng(4)
+    xs, ss, cs, xn = [], [], [], []
+    keep = []
+    for i in range(40):
+        n = int(rng.integers(1, 20000))
+        a = mixed_angles(n, seed=100 + i)
+        bx = torch.zeros(n + 4, device="cuda")
+        bs = torch.zeros(n + 4, device="cuda")
+        bc = torch.zeros(n + 4, device="cuda")
+        ox, os_, oc = (int(v) for v in rng.integers(0, 4, 3))
+        bx[ox:ox + n] = torch.from_numpy(a).cuda()
+        xs.append(bx[ox:ox + n]); ss.append(bs[os_:os_ + n]); cs.append(bc[oc:oc + n])
+        xn.append(a)
+        keep += [bx, bs, bc]
+    segs, lens = api.segments_from_lists(xs, ss, cs)
+    api.sincos_batched(segs, lens)
+    torch.cuda.synchronize()
+    for i, a in enumerate(xn):
+        want_s, want_c = oracle.sincos(a)
+        assert_f32_parity(as_np(ss[i]), want_s, f"seg {i} s")
+        assert_f32_parity(as_np(cs[i]), want_c, f"seg {i} c")
+
+
+def test_graph_replay_bit_identical(cuda_lib):
+    lens = EDGE_LENS * 3
+    x, xt, s, c, offs = packed(lens, "f32", seed=3)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    with api.BatchedGraph(segs, lens_t) as g:
+        g.launch()
+        torch.cuda.synchronize()
+        check_all(x, s, c, "f32", "plain", "normalized", "graph replay 1")
+        first_s, first_c = as_np(s).copy(), as_np(c).copy()
+        s.fill_(0)
+        c.fill_(0)
+        before = api.sincos_launch_count()
+        g.launch()
+        torch.cuda.synchronize()
+        assert api.sincos_launch_count() == before + 2
+        assert np.array_equal(as_np(s).view(np.uint32), first_s.view(np.uint32))
+        assert np.array_equal(as_np(c).view(np.uint32), first_c.view(np.uint32))
+
+
+def test_batching_workload_full_size(cuda_lib):
+    """4096 arrays, lengths log-uniform in [1, 2^20] (seed 3), packed back to
+    back: the persistent launch, its graph replay and 4096 single-array
+    launches agree bit for bit; the oracle checks the first and last 64 and
+    64 random elements of every array."""
+    b = workloads.batching()
+    xt = torch.from_numpy(b.angles).cuda()
+    s = torch.empty_like(xt)
+    c = torch.empty_like(xt)
+    segs, lens = api.segments(xt, s, c, b.offsets, b.lens)
+    api.sincos_batched(segs, lens)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    idx = []
+    for off, n in zip(b.offsets, b.lens):
+        k = min(int(n), 64)
+        idx.append(off + np.arange(k))
+        idx.append(off + n - k + np.arange(k))
+        idx.append(off + rng.integers(0, n, 64))
+    idx = np.unique(np.concatenate(idx))
+    it = torch.from_numpy(idx).cuda()
+    want_s, want_c = oracle.sincos(b.angles[idx])
+    assert_f32_parity(as_np(s[it]), want_s, "batched s")
+    assert_f32_parity(as_np(c[it]), want_c, "batched c")
+
+    s2 = torch.empty_like(xt)
+    c2 = torch.empty_like(xt)
+    segs2, _ = api.segments(xt, s2, c2, b.offsets, b.lens)
+    with api.BatchedGraph(segs2, lens) as g:
+        g.launch()
+    torch.cuda.synchronize()
+    assert torch.equal(s.view(torch.int32), s2.view(torch.int32))
+    assert torch.equal(c.view(torch.int32), c2.view(torch.int32))
+
+    s3 = torch.empty_like(xt)
+    c3 = torch.empty_like(xt)
+    for off, n in zip(b.offsets.tolist(), b.lens.tolist()):
+        api.sincos_pairs(xt[off:off + n], s3[off:off + n], c3[off:off + n])
+    torch.cuda.synchronize()
+    assert torch.equal(s.view(torch.int32), s3.view(torch.int32))
+    assert torch.equal(c.view(torch.int32), c3.view(torch.int32))

@@ -1,0 +1,113 @@
+"""Host-buffer path, autotuner and plan cache, on the GPU."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import as_np, assert_16_parity, assert_f32_parity, mixed_angles
+from paper_cs_0406049_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_path_chunks(cuda_lib, dtype, pinned):
+    """Many chunks (a small workspace), a ragged last chunk, host arrays."""
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    n = (1 << 20) + 12345
+    x = mixed_angles(n, seed=9)
+    xh = torch.from_numpy(x)
+    sh = torch.empty(n, dtype=tdt)
+    ch = torch.empty(n, dtype=tdt)
+    if pinned:
+        xh, sh, ch = xh.pin_memory(), sh.pin_memory(), ch.pin_memory()
+    ws = torch.empty(api.sincos_host_workspace_bytes(dtype, 100000), dtype=torch.uint8,
+                     device="cuda")
+    api.sincos_pairs_host(xh, sh, ch, ws, "compensated")
+    torch.cuda.synchronize()
+    want_s, want_c = oracle.sincos(x, reduction="compensated", out=dtype)
+    if dtype == "f32":
+        assert_f32_parity(sh.numpy(), want_s, "host s")
+        assert_f32_parity(ch.numpy(), want_c, "host c")
+    else:
+        assert_16_parity(as_np(sh), want_s, dtype == "bf16", "host s")
+        assert_16_parity(as_np(ch), want_c, dtype == "bf16", "host c")
+
+
+def test_autotune_pairs_and_plan_cache(cuda_lib, tmp_path):
+    n = 1 << 22
+    x = mixed_angles(n, seed=10)
+    xt = torch.from_numpy(x).cuda()
+    s = torch.empty_like(xt)
+    c = torch.empty_like(xt)
+    best = api.sincos_autotune_pairs(xt, s, c)
+    assert best["block"] in (128, 256, 512, 1024)
+    assert api.sincos_plan_get("pairs", "f32", n) == best
+    s.zero_()
+    c.zero_()
+    api.sincos_pairs(xt, s, c)
+    want_s, want_c = oracle.sincos(x)
+    assert_f32_parity(as_np(s), want_s, "tuned s")
+    assert_f32_parity(as_np(c), want_c, "tuned c")
+
+    path = str(tmp_path / "plans.json")
+    api.sincos_plan_cache_save(path)
+    api.sincos_plan_set("pairs", "f32", n, 128, 1, 2)
+    assert api.sincos_plan_get("pairs", "f32", n) == {"block": 128, "unroll": 1, "ctas_per_sm": 2}
+    api.sincos_plan_cache_load(path)
+    assert api.sincos_plan_get("pairs", "f32", n) == best
+    assert os.path.getsize(path) > 0
+
+
+@pytest.mark.parametrize("plan", [(64, 1, 1), (128, 8, 16), (1024, 8, 2), (96, 2, 3)])
+def test_every_plan_shape_is_exact(cuda_lib, plan):
+    """Odd plans (small grids, big unrolls, non-power-of-two blocks) change
+    only the schedule, never the results."""
+    n = 777777
+    x = mixed_angles(n, seed=11)
+    xt = torch.from_numpy(x).cuda()
+    want_s, want_c = oracle.sincos(x)
+    for op in ("pairs", "batched"):
+        key = n if op == "pairs" else 3
+        old = api.sincos_plan_get(op, "f32", key)
+        api.sincos_plan_set(op, "f32", key, *plan)
+        try:
+            s = torch.empty_like(xt)
+            c = torch.empty_like(xt)
+            if op == "pairs":
+                api.sincos_pairs(xt, s, c)
+            else:
+                offs = [0, 1000, 1001]
+                lens = [1000, 1, n - 1001]
+                segs, lens_t = api.segments(xt, s, c, offs, lens)
+                api.sincos_batched(segs, lens_t)
+            assert_f32_parity(as_np(s), want_s, f"{op} {plan} s")
+            assert_f32_parity(as_np(c), want_c, f"{op} {plan} c")
+        finally:
+            api.sincos_plan_set(op, "f32", key, old["block"], old["unroll"], old["ctas_per_sm"])
+
+
+def test_autotune_backward_and_batched(cuda_lib):
+    n = 1 << 21
+    rng = np.random.default_rng(12)
+    g = [torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda() for _ in range(4)]
+    gx = torch.empty(n, device="cuda")
+    p = api.sincos_autotune_backward(g[0], g[1], g[2], g[3], gx)
+    assert p["unroll"] in (1, 2, 4, 8)
+    lens = [1000, 50000, 3, 70000]
+    total = sum(lens)
+    x = mixed_angles(total, seed=13)
+    xt = torch.from_numpy(x).cuda()
+    s = torch.empty_like(xt)
+    c = torch.empty_like(xt)
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    p = api.sincos_autotune_batched(segs, lens_t)
+    assert api.sincos_plan_get("batched", "f32", len(lens)) == p
+    s.zero_()
+    api.sincos_batched(segs, lens_t)
+    want_s, _ = oracle.sincos(x)
+    assert_f32_parity(as_np(s), want_s, "batched after tuning")
