@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--autotune", action="store_true", help="tune the launch plan first")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="time the library's default plans instead of tuning each op first")
     return p.parse_args()
 
 
@@ -313,7 +314,7 @@ def cpu_baseline(x: np.ndarray) -> dict:
                       f"{dt:.1f} s wall on {used} threads"}
 
 
-def extras(torch, api, workloads, dist, steps_hint: int) -> dict:
+def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict:
     """Secondary workloads, each with its own GB/s and errors (not the headline)."""
     out = {}
     k = max(20, min(steps_hint, 200))
@@ -331,13 +332,16 @@ def extras(torch, api, workloads, dist, steps_hint: int) -> dict:
                           ("f16_compensated", torch.float16, "compensated")):
         s = torch.empty(x.size, dtype=dt, device="cuda")
         c = torch.empty_like(s)
+        if autotune:
+            api.sincos_autotune_pairs(xt, s, c, red)
         total, per, _ = time_loop(torch, lambda: api.sincos_pairs_ex(xt, s, c, red), k, 3, dist)
         bytes_ = x.size * (4 + 2 * s.element_size())
         ms = statistics.mean(per)
         err = fp64_errors(x[idx.cpu().numpy()], s[idx].float().cpu().numpy().astype(np.float64),
                           c[idx].float().cpu().numpy().astype(np.float64))
         prec[name] = {"pairs_per_s": x.size / (ms * 1e-3), "gbs": bytes_ / (ms * 1e-3) / 1e9,
-                      "frac_of_peak": bytes_ / (ms * 1e-3) / 1e9 / peak, "ms": ms, "errors": err}
+                      "frac_of_peak": bytes_ / (ms * 1e-3) / 1e9 / peak, "ms": ms, "errors": err,
+                      "plan": api.sincos_plan_get("pairs", dt, x.size)}
         del s, c
     out["precision_2p26"] = prec
     del xt
@@ -351,9 +355,12 @@ def extras(torch, api, workloads, dist, steps_hint: int) -> dict:
     c = torch.empty_like(xt)
     api.sincos_pairs(xt, s, c)
     gx = torch.empty_like(xt)
+    if autotune:
+        api.sincos_autotune_backward(gs, gc, s, c, gx)
     total, per, _ = time_loop(torch, lambda: api.sincos_backward(gs, gc, s, c, gx), k, 3, dist)
     ms = statistics.mean(per)
-    bwd = {"gbs": 20 * xt.numel() / (ms * 1e-3) / 1e9, "ms": ms}
+    bwd = {"gbs": 20 * xt.numel() / (ms * 1e-3) / 1e9, "ms": ms,
+           "plan": api.sincos_plan_get("backward", "f32", xt.numel())}
     bwd["frac_of_peak"] = bwd["gbs"] / peak
     xg = xt.clone().requires_grad_(True)
 
@@ -375,6 +382,9 @@ def extras(torch, api, workloads, dist, steps_hint: int) -> dict:
     segs, lens = api.segments(xt, s, c, b.offsets, b.lens)
     bytes_ = BYTES_PER_PAIR * b.total
     bat = {"total_pairs": b.total, "count": b.count}
+    if autotune:
+        api.sincos_autotune_batched(segs, lens)
+    bat["plan"] = api.sincos_plan_get("batched", "f32", b.count)
     total, per, _ = time_loop(torch, lambda: api.sincos_batched(segs, lens), k, 3, dist)
     bat["persistent_gbs"] = bytes_ / (statistics.mean(per) * 1e-3) / 1e9
     g = api.BatchedGraph(segs, lens)
@@ -425,7 +435,7 @@ def run_ours(args, dist: Dist):
     x = torch.from_numpy(x_np).cuda()
     s = torch.empty_like(x)
     c = torch.empty_like(x)
-    if args.autotune:
+    if not args.no_autotune:
         api.sincos_autotune_pairs(x, s, c)
     plan = api.sincos_plan_get("pairs", "f32", n)
 
@@ -481,11 +491,17 @@ def run_ours(args, dist: Dist):
     ext = None
     if not args.no_extras:
         del s, c
-        ext = extras(torch, api, workloads, dist, args.steps)
+        ext = extras(torch, api, workloads, dist, args.steps, not args.no_autotune)
 
     cpu = None
     if dist.rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x_np)
+
+    if ext is not None:
+        # the batched and backward forms against the headline kernel's GB/s
+        ext["batching_4096"]["graph_vs_forward_gbs"] = ext["batching_4096"]["graph_gbs"] / achieved
+        ext["differentiation_2p26"]["backward_vs_forward_gbs"] = \
+            ext["differentiation_2p26"]["gbs"] / achieved
 
     if dist.rank == 0:
         line = {

@@ -190,15 +190,16 @@ size_t sincos_host_workspace_bytes(int out_dtype, int64_t chunk_elems);
 
 typedef enum { SINCOS_OP_PAIRS = 0, SINCOS_OP_BACKWARD = 1, SINCOS_OP_BATCHED = 2 } sincos_op;
 
-/* A launch configuration: threads per CTA, vectors each thread keeps in
- * flight per iteration (16-byte loads), and resident CTAs per SM that the
- * grid is sized for.  A batched tile is block * unroll * vector-width
- * elements. */
+/* A launch configuration: threads per CTA, output vectors each thread
+ * keeps in flight per iteration, resident CTAs per SM that the grid is sized
+ * for, and the bytes of output one thread writes per vector and per array
+ * (16: st.v4; 32: 256-bit st.v8).  A vector holds vec_bytes / sizeof(out)
+ * pairs, and a batched tile is block * unroll of them. */
 typedef struct {
     int block;        /* 64 .. 1024, multiple of 32 */
     int unroll;       /* 1, 2, 4 or 8 */
     int ctas_per_sm;  /* 1 .. 32 */
-    int reserved;     /* 0 */
+    int vec_bytes;    /* 16 or 32; 0 selects 32 */
 } sincos_plan;
 
 /* The plan used for (op, out_dtype, n) on the current device: the tuned one

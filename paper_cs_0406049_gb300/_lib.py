@@ -22,10 +22,11 @@ OP_PAIRS, OP_BACKWARD, OP_BATCHED = 0, 1, 2
 
 class sincos_plan(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("unroll", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("ctas_per_sm", ctypes.c_int), ("vec_bytes", ctypes.c_int)]
 
     def as_dict(self):
-        return {"block": self.block, "unroll": self.unroll, "ctas_per_sm": self.ctas_per_sm}
+        return {"block": self.block, "unroll": self.unroll, "ctas_per_sm": self.ctas_per_sm,
+                "vec_bytes": self.vec_bytes if self.vec_bytes else 32}
 
 
 class sincos_seg(ctypes.Structure):

@@ -211,8 +211,9 @@ def sincos_plan_get(op: str, out_dtype, n: int) -> dict:
     return p.as_dict()
 
 
-def sincos_plan_set(op: str, out_dtype, n: int, block: int, unroll: int, ctas_per_sm: int):
-    p = _lib.sincos_plan(block, unroll, ctas_per_sm, 0)
+def sincos_plan_set(op: str, out_dtype, n: int, block: int, unroll: int, ctas_per_sm: int,
+                    vec_bytes: int = 32):
+    p = _lib.sincos_plan(block, unroll, ctas_per_sm, vec_bytes)
     check(lib().sincos_plan_set(_OPS[op], _DTYPES[_torch_dtype(out_dtype)], n, ctypes.byref(p)),
           "sincos_plan_set")
 

@@ -99,6 +99,17 @@ int resident_ctas(const void *kernel, int block, int want)
     return per_sm < want ? per_sm : want;
 }
 
+sincos_plan fit_plan(const void *kernel, const sincos_plan &plan, int *per_sm)
+{
+    sincos_plan p = plan;
+    *per_sm = resident_ctas(kernel, p.block, p.ctas_per_sm);
+    while (*per_sm <= 0 && p.block > 32) {
+        p.block = (p.block / 2 + 31) / 32 * 32;
+        *per_sm = resident_ctas(kernel, p.block, p.ctas_per_sm);
+    }
+    return p;
+}
+
 bool valid_dtype(int d) { return d == SINCOS_F32 || d == SINCOS_BF16 || d == SINCOS_F16; }
 bool valid_reduction(int r) { return r == SINCOS_RED_PLAIN || r == SINCOS_RED_COMPENSATED; }
 bool valid_coef(int c) { return c == SINCOS_COEF_NORMALIZED || c == SINCOS_COEF_DAGGER; }

@@ -104,17 +104,6 @@ __device__ __forceinline__ void pair(float x, float &s, float &c)
 // Output element types.
 // ---------------------------------------------------------------------------
 
-template <class OutT> struct Out;
-template <> struct Out<float> {
-    static constexpr int kVec = 4;   // elements per 16-byte output vector
-};
-template <> struct Out<__nv_bfloat16> {
-    static constexpr int kVec = 8;
-};
-template <> struct Out<__half> {
-    static constexpr int kVec = 8;
-};
-
 __device__ __forceinline__ void store_elem(float *p, float v) { *p = v; }
 __device__ __forceinline__ void store_elem(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void store_elem(__half *p, float v) { *p = __float2half_rn(v); }
@@ -133,92 +122,109 @@ __device__ __forceinline__ uint32_t pack2(__half *, float lo, float hi)
 }
 
 // ---------------------------------------------------------------------------
-// 16-byte global memory access.  Loads bypass L1 allocation (every byte is
-// used once); stores are marked evict-first (.cs) so the output stream does
-// not push the input out of L2.
+// Vector global memory access.  A thread moves W = 16 or 32 bytes of output
+// per vector (one st.v4 or one 256-bit st.v8), i.e. E = W / sizeof(OutT)
+// pairs, reading their 4E bytes of angles with 16- or 32-byte loads.
+//   loads   ld.global.nc.L1::no_allocate: every byte is used once, so no L1
+//           allocation; the non-coherent path is used only when the kernel
+//           does not write the input (LD_COHERENT otherwise).
+//   stores  16-byte: st.global.cs (evict-first streaming store);
+//           32-byte: st.global.L1::no_allocate.L2::evict_first.v8 -- the
+//           256-bit form that sm_100-class GPUs accept with an L2 eviction
+//           priority, so the output stream leaves L2 first.
 // ---------------------------------------------------------------------------
 
 enum { LD_NC = 0, LD_COHERENT = 1 };
 
 template <int LD>
-__device__ __forceinline__ float4 ld16(const float *p)
+__device__ __forceinline__ void ld16(float *d, const float *p)
 {
-    float4 v;
     if (LD == LD_NC)
         asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]) : "l"(p));
     else
         asm("ld.global.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-    return v;
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]) : "l"(p));
 }
-
-__device__ __forceinline__ void st16(void *p, float a, float b, float c, float d)
-{
-    asm volatile("st.global.cs.v4.f32 [%0], {%1,%2,%3,%4};"
-                 :: "l"(p), "f"(a), "f"(b), "f"(c), "f"(d));
-}
-
-__device__ __forceinline__ void st16u(void *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
-{
-    asm volatile("st.global.cs.v4.b32 [%0], {%1,%2,%3,%4};"
-                 :: "l"(p), "r"(a), "r"(b), "r"(c), "r"(d));
-}
-
-// ---------------------------------------------------------------------------
-// One output vector: Out<OutT>::kVec angles in (one or two 16-byte loads),
-// the same number of sines and cosines out (one 16-byte store each).
-// ---------------------------------------------------------------------------
-
-template <class OutT> struct InVec;
-template <> struct InVec<float> { float4 a; };
-template <> struct InVec<__nv_bfloat16> { float4 a, b; };
-template <> struct InVec<__half> { float4 a, b; };
 
 template <int LD>
-__device__ __forceinline__ void load_vec(InVec<float> &v, const float *x) { v.a = ld16<LD>(x); }
-template <int LD>
-__device__ __forceinline__ void load_vec(InVec<__nv_bfloat16> &v, const float *x)
+__device__ __forceinline__ void ld32(float *d, const float *p)
 {
-    v.a = ld16<LD>(x);
-    v.b = ld16<LD>(x + 4);
-}
-template <int LD>
-__device__ __forceinline__ void load_vec(InVec<__half> &v, const float *x)
-{
-    v.a = ld16<LD>(x);
-    v.b = ld16<LD>(x + 4);
+    if (LD == LD_NC)
+        asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]),
+              "=f"(d[6]), "=f"(d[7]) : "l"(p));
+    else
+        asm("ld.global.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3]), "=f"(d[4]), "=f"(d[5]),
+              "=f"(d[6]), "=f"(d[7]) : "l"(p));
 }
 
-// Compute the pairs of one input vector and store one 16-byte vector of
-// sines and one of cosines.
-template <int RED, int COEF, class OutT>
-__device__ __forceinline__ void compute_store(const InVec<OutT> &v, OutT *s, OutT *c)
+// NB bytes of binary32 values (16, 32 or 64) into d[0 .. NB/4).
+template <int NB, int LD>
+__device__ __forceinline__ void load_f32(float *d, const float *p)
 {
-    if constexpr (Out<OutT>::kVec == 4) {
-        float s0, s1, s2, s3, c0, c1, c2, c3;
-        pair<RED, COEF>(v.a.x, s0, c0);
-        pair<RED, COEF>(v.a.y, s1, c1);
-        pair<RED, COEF>(v.a.z, s2, c2);
-        pair<RED, COEF>(v.a.w, s3, c3);
-        st16(s, s0, s1, s2, s3);
-        st16(c, c0, c1, c2, c3);
+    if constexpr (NB == 16) {
+        ld16<LD>(d, p);
     } else {
-        float sv[8], cv[8];
-        pair<RED, COEF>(v.a.x, sv[0], cv[0]);
-        pair<RED, COEF>(v.a.y, sv[1], cv[1]);
-        pair<RED, COEF>(v.a.z, sv[2], cv[2]);
-        pair<RED, COEF>(v.a.w, sv[3], cv[3]);
-        pair<RED, COEF>(v.b.x, sv[4], cv[4]);
-        pair<RED, COEF>(v.b.y, sv[5], cv[5]);
-        pair<RED, COEF>(v.b.z, sv[6], cv[6]);
-        pair<RED, COEF>(v.b.w, sv[7], cv[7]);
-        OutT *tag = nullptr;
-        st16u(s, pack2(tag, sv[0], sv[1]), pack2(tag, sv[2], sv[3]), pack2(tag, sv[4], sv[5]),
-              pack2(tag, sv[6], sv[7]));
-        st16u(c, pack2(tag, cv[0], cv[1]), pack2(tag, cv[2], cv[3]), pack2(tag, cv[4], cv[5]),
-              pack2(tag, cv[6], cv[7]));
+#pragma unroll
+        for (int k = 0; k < NB / 32; ++k) ld32<LD>(d + 8 * k, p + 8 * k);
     }
+}
+
+template <int W>
+__device__ __forceinline__ void store_words(void *p, const uint32_t *w)
+{
+    if constexpr (W == 16)
+        asm volatile("st.global.cs.v4.b32 [%0], {%1,%2,%3,%4};"
+                     :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]));
+    else
+        asm volatile("st.global.L1::no_allocate.L2::evict_first.v8.b32 [%0], "
+                     "{%1,%2,%3,%4,%5,%6,%7,%8};"
+                     :: "l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]),
+                        "r"(w[5]), "r"(w[6]), "r"(w[7]));
+}
+
+// Pairs per vector for an output type and access width.
+template <class OutT, int W>
+struct Vec {
+    static constexpr int E = W / (int)sizeof(OutT);        // pairs per vector
+    static constexpr int IN_BYTES = 4 * E;                 // angle bytes per vector
+    static constexpr int IN_ALIGN = IN_BYTES < 32 ? IN_BYTES : 32;
+};
+
+template <class OutT, int W, int LD>
+__device__ __forceinline__ void load_vec(float *in, const float *x)
+{
+    load_f32<Vec<OutT, W>::IN_BYTES, LD>(in, x);
+}
+
+// The pairs of one vector of angles, stored as one W-byte vector of sines
+// and one of cosines.
+template <int RED, int COEF, class OutT, int W>
+__device__ __forceinline__ void compute_store(const float *in, OutT *s, OutT *c)
+{
+    constexpr int E = Vec<OutT, W>::E;
+    float sv[E], cv[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) pair<RED, COEF>(in[i], sv[i], cv[i]);
+    uint32_t ws[W / 4], wc[W / 4];
+    if constexpr (sizeof(OutT) == 4) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            ws[i] = __float_as_uint(sv[i]);
+            wc[i] = __float_as_uint(cv[i]);
+        }
+    } else {
+        OutT *tag = nullptr;
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) {
+            ws[k] = pack2(tag, sv[2 * k], sv[2 * k + 1]);
+            wc[k] = pack2(tag, cv[2 * k], cv[2 * k + 1]);
+        }
+    }
+    store_words<W>(s, ws);
+    store_words<W>(c, wc);
 }
 
 template <int RED, int COEF, class OutT>
@@ -230,18 +236,49 @@ __device__ __forceinline__ void scalar_elem(const float *x, OutT *s, OutT *c, in
     store_elem(c + i, cv);
 }
 
-// Smallest h in [0, kVec) such that x + h, s + h and c + h are all 16-byte
-// aligned, or -1 if the three pointers admit no common vector alignment.
-template <class OutT>
-__host__ __device__ __forceinline__ int vector_head(const void *x, const void *s, const void *c)
+// Smallest h in [0, E) such that x + h meets the angle loads' alignment and
+// s + h, c + h are W-byte aligned, or -1 if the three pointers admit no
+// common vector alignment.
+template <class OutT, int W>
+__host__ __device__ __forceinline__ int vector_w_head(const void *x, const void *s, const void *c)
 {
+    using V = Vec<OutT, W>;
     const uintptr_t ax = (uintptr_t)x, as = (uintptr_t)s, ac = (uintptr_t)c;
-    for (int h = 0; h < Out<OutT>::kVec; ++h) {
-        if (((ax + 4u * h) & 15u) == 0 && ((as + sizeof(OutT) * h) & 15u) == 0 &&
-            ((ac + sizeof(OutT) * h) & 15u) == 0)
+    for (int h = 0; h < V::E; ++h) {
+        if (((ax + 4u * h) % V::IN_ALIGN) == 0 && ((as + sizeof(OutT) * h) % W) == 0 &&
+            ((ac + sizeof(OutT) * h) % W) == 0)
             return h;
     }
     return -1;
+}
+
+// Smallest h such that x + h, s + h and c + h all start a 128-byte L2 line,
+// or -1 if their offsets within a line differ.  Starting the vector grid on
+// line boundaries means every warp-wide vector store covers whole lines, so
+// no line is written in two halves by different warps at different times.
+template <class OutT>
+__host__ __device__ __forceinline__ int line_head(const void *x, const void *s, const void *c)
+{
+    constexpr unsigned osz = sizeof(OutT);
+    const unsigned ax = (unsigned)((uintptr_t)x & 127u);
+    const unsigned as = (unsigned)((uintptr_t)s & 127u);
+    const unsigned ac = (unsigned)((uintptr_t)c & 127u);
+    if ((ax & 3u) || (as % osz) || (ac % osz)) return -1;
+    const unsigned hs = ((128u - as) & 127u) / osz;
+    const unsigned hc = ((128u - ac) & 127u) / osz;
+    const unsigned hx = ((128u - ax) & 127u) / 4u;        // h = hx (mod 32)
+    if (hs != hc || (hs & 31u) != hx) return -1;
+    return (int)hs;
+}
+
+// Where the vector grid of an array triple starts: on a 128-byte line if the
+// three pointers allow it (h < 128 / sizeof(OutT)), else at the first W-byte
+// vector boundary (h < E), else -1 (no common vector alignment).
+template <class OutT, int W>
+__host__ __device__ __forceinline__ int vector_head(const void *x, const void *s, const void *c)
+{
+    const int h = line_head<OutT>(x, s, c);
+    return h >= 0 ? h : vector_w_head<OutT, W>(x, s, c);
 }
 
 }  // namespace sincos_gb300

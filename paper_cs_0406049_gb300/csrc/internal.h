@@ -32,6 +32,10 @@ void count_launches(uint64_t k);
 // Resident CTAs per SM of `kernel` at `block` threads (cached), capped by the
 // plan's request; at least 1 when the kernel fits at all, 0 when it does not.
 int resident_ctas(const void *kernel, int block, int want);
+// The plan with its CTA size halved (down to 32 threads) until `kernel` fits
+// on an SM at all; *per_sm receives the resident CTAs per SM to size the grid
+// for (0 if nothing fits).
+sincos_plan fit_plan(const void *kernel, const sincos_plan &plan, int *per_sm);
 
 bool valid_dtype(int d);
 bool valid_reduction(int r);
@@ -41,6 +45,8 @@ inline int dtype_size(int d) { return d == SINCOS_F32 ? 4 : 2; }
 // Plan lookup (tuned or default) for the current device.
 sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n);
 bool plan_valid(const sincos_plan &p);
+// Bytes each thread moves per output vector (16 or 32); 0 in a plan means 32.
+inline int plan_vec_bytes(const sincos_plan &p) { return p.vec_bytes == 16 ? 16 : 32; }
 
 // Kernel launchers.  Arguments are already validated; they enqueue on `st`
 // and return a status.

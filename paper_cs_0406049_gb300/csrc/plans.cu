@@ -1,8 +1,8 @@
 // plans.cu -- launch plans: defaults, the tuned-plan cache (in memory and as
 // a JSON file) and the autotuner that fills it.
 //
-// A plan is (threads per CTA, 16-byte vectors in flight per thread, resident
-// CTAs per SM).  Plans are keyed by device ("<name>:<SMs>"), operation,
+// A plan is (threads per CTA, vectors in flight per thread, resident CTAs per
+// SM, bytes per vector access).  Plans are keyed by device ("<name>:<SMs>"), operation,
 // output dtype and the bit length of the element count, so one tuning run
 // per size class covers every later call in that class.
 #include <algorithm>
@@ -44,11 +44,13 @@ std::string device_key(const DeviceInfo &dev)
 
 sincos_plan default_plan(int op, int dtype)
 {
-    // 2048 resident threads per SM with several 16-byte loads each keeps
-    // enough bytes in flight to cover HBM latency on every SM.
-    if (op == SINCOS_OP_BACKWARD) return sincos_plan{256, 2, 8, 0};
-    if (dtype == SINCOS_F32) return sincos_plan{256, 4, 8, 0};
-    return sincos_plan{256, 2, 8, 0};
+    // Fastest plans of a GB300 sweep (2^26..2^28 elements, 4096-array batch).
+    // About 1024 resident threads per SM with 2..8 vectors in flight each
+    // beat full occupancy: fewer concurrent streams keep DRAM pages open.
+    if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
+    if (dtype != SINCOS_F32) return sincos_plan{256, 2, 4, 32};
+    if (op == SINCOS_OP_BATCHED) return sincos_plan{1024, 2, 1, 16};
+    return sincos_plan{256, 8, 4, 16};
 }
 
 int load_file(const char *path);
@@ -100,7 +102,7 @@ int load_file(const char *path)
         if (*p != '{') break;
         ++p;
         std::string device;
-        long op = -1, dtype = -1, bucket = -1, block = 0, unroll = 0, ctas = 0;
+        long op = -1, dtype = -1, bucket = -1, block = 0, unroll = 0, ctas = 0, vec = 0;
         for (;;) {
             skip_ws(p);
             if (*p == '}') {
@@ -128,9 +130,10 @@ int load_file(const char *path)
                 else if (key == "block") block = v;
                 else if (key == "unroll") unroll = v;
                 else if (key == "ctas_per_sm") ctas = v;
+                else if (key == "vec_bytes") vec = v;
             }
         }
-        sincos_plan plan{(int)block, (int)unroll, (int)ctas, 0};
+        sincos_plan plan{(int)block, (int)unroll, (int)ctas, (int)vec};
         if (device.empty() || op < 0 || dtype < 0 || bucket < 0 || !plan_valid(plan))
             return SINCOS_EINVAL;
         loaded[PlanKey(device, (int)op, (int)dtype, (int)bucket)] = plan;
@@ -150,10 +153,12 @@ std::vector<sincos_plan> candidates(const DeviceInfo &dev)
 {
     std::vector<sincos_plan> out;
     const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
-    for (int block : {128, 256, 512, 1024})
-        for (int unroll : {1, 2, 4, 8})
-            for (int ctas : {1, 2, 4, 8, 16})
-                if (block * ctas <= max_threads) out.push_back(sincos_plan{block, unroll, ctas, 0});
+    for (int vec : {16, 32})
+        for (int block : {128, 256, 512, 1024})
+            for (int unroll : {1, 2, 4, 8})
+                for (int ctas : {1, 2, 4, 8, 16})
+                    if (block * ctas <= max_threads)
+                        out.push_back(sincos_plan{block, unroll, ctas, vec});
     return out;
 }
 
@@ -227,7 +232,8 @@ bool plan_valid(const sincos_plan &p)
 {
     return p.block >= 64 && p.block <= 1024 && p.block % 32 == 0 &&
            (p.unroll == 1 || p.unroll == 2 || p.unroll == 4 || p.unroll == 8) &&
-           p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32;
+           p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32 &&
+           (p.vec_bytes == 0 || p.vec_bytes == 16 || p.vec_bytes == 32);
 }
 
 sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n)
@@ -350,10 +356,10 @@ int sincos_plan_cache_save(const char *path)
         }
         std::fprintf(f,
                      "%s\n  {\"device\": \"%s\", \"op\": %d, \"dtype\": %d, \"bucket\": %d, "
-                     "\"block\": %d, \"unroll\": %d, \"ctas_per_sm\": %d}",
+                     "\"block\": %d, \"unroll\": %d, \"ctas_per_sm\": %d, \"vec_bytes\": %d}",
                      first ? "" : ",", dev.c_str(), std::get<1>(kv.first), std::get<2>(kv.first),
                      std::get<3>(kv.first), kv.second.block, kv.second.unroll,
-                     kv.second.ctas_per_sm);
+                     kv.second.ctas_per_sm, plan_vec_bytes(kv.second));
         first = false;
     }
     std::fprintf(f, "\n]}\n");

@@ -1,0 +1,64 @@
+"""Run one kernel of the library a few times on a synthetic case, for profilers.
+
+    python -m paper_cs_0406049_gb300.profile_case --op forward --log2n 26 --launches 3
+
+Generates the inputs on the device (uniform angles in [-1000, 1000) or N(0, 1)
+gradients from a seeded torch generator), launches the chosen entry point
+``--launches`` times on the current stream and exits.  The sizes are meant for
+profiler captures: large enough to exceed the L2 cache, small enough to keep
+device memory and capture time modest.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+import torch
+
+from . import api, build
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--op", choices=["forward", "forward_bf16", "forward_compensated",
+                                    "backward", "batched"], default="forward")
+    p.add_argument("--log2n", type=int, default=26)
+    p.add_argument("--launches", type=int, default=3)
+    a = p.parse_args(argv)
+    build.build()
+    n = 1 << a.log2n
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = (torch.rand(n, device="cuda", generator=g) * 2000.0 - 1000.0).contiguous()
+    if a.op.startswith("forward"):
+        dt = torch.bfloat16 if a.op == "forward_bf16" else torch.float32
+        red = "compensated" if a.op == "forward_compensated" else "plain"
+        s = torch.empty(n, dtype=dt, device="cuda")
+        c = torch.empty_like(s)
+        run = lambda: api.sincos_pairs_ex(x, s, c, red)
+    elif a.op == "backward":
+        gs = torch.randn(n, device="cuda", generator=g)
+        gc = torch.randn(n, device="cuda", generator=g)
+        s = torch.empty_like(x)
+        c = torch.empty_like(x)
+        api.sincos_pairs(x, s, c)
+        gx = torch.empty_like(x)
+        run = lambda: api.sincos_backward(gs, gc, s, c, gx)
+    else:
+        # 4096 segments of pseudo-random lengths packed into the n angles
+        lens = torch.randint(1, 2 * (n // 4096), (4096,), generator=g, device="cuda")
+        lens = (lens * n // int(lens.sum())).clamp(min=1).cpu()
+        offs = torch.cumsum(lens, 0) - lens
+        keep = offs + lens <= n
+        s = torch.empty_like(x)
+        c = torch.empty_like(x)
+        segs, lens_t = api.segments(x, s, c, offs[keep].numpy(), lens[keep].numpy())
+        run = lambda: api.sincos_batched(segs, lens_t)
+    for _ in range(a.launches):
+        run()
+    torch.cuda.synchronize()
+    print(f"profile_case {a.op} n=2^{a.log2n} launches={a.launches} ok")
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

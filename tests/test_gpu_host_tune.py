@@ -55,14 +55,16 @@ def test_autotune_pairs_and_plan_cache(cuda_lib, tmp_path):
 
     path = str(tmp_path / "plans.json")
     api.sincos_plan_cache_save(path)
-    api.sincos_plan_set("pairs", "f32", n, 128, 1, 2)
-    assert api.sincos_plan_get("pairs", "f32", n) == {"block": 128, "unroll": 1, "ctas_per_sm": 2}
+    api.sincos_plan_set("pairs", "f32", n, 128, 1, 2, 16)
+    assert api.sincos_plan_get("pairs", "f32", n) == {"block": 128, "unroll": 1, "ctas_per_sm": 2,
+                                                      "vec_bytes": 16}
     api.sincos_plan_cache_load(path)
     assert api.sincos_plan_get("pairs", "f32", n) == best
     assert os.path.getsize(path) > 0
 
 
-@pytest.mark.parametrize("plan", [(64, 1, 1), (128, 8, 16), (1024, 8, 2), (96, 2, 3)])
+@pytest.mark.parametrize("plan", [(64, 1, 1, 16), (128, 8, 16, 32), (1024, 8, 2, 32),
+                                  (96, 2, 3, 16), (256, 4, 4, 32)])
 def test_every_plan_shape_is_exact(cuda_lib, plan):
     """Odd plans (small grids, big unrolls, non-power-of-two blocks) change
     only the schedule, never the results."""
@@ -87,7 +89,8 @@ def test_every_plan_shape_is_exact(cuda_lib, plan):
             assert_f32_parity(as_np(s), want_s, f"{op} {plan} s")
             assert_f32_parity(as_np(c), want_c, f"{op} {plan} c")
         finally:
-            api.sincos_plan_set(op, "f32", key, old["block"], old["unroll"], old["ctas_per_sm"])
+            api.sincos_plan_set(op, "f32", key, old["block"], old["unroll"], old["ctas_per_sm"],
+                                old["vec_bytes"])
 
 
 def test_autotune_backward_and_batched(cuda_lib):
