@@ -24,9 +24,17 @@ def main(argv=None):
                                     "backward", "batched"], default="forward")
     p.add_argument("--log2n", type=int, default=26)
     p.add_argument("--launches", type=int, default=3)
+    p.add_argument("--plan", default="",
+                   help="block,unroll,ctas_per_sm,vec_bytes to use instead of the default plan")
     a = p.parse_args(argv)
     build.build()
     n = 1 << a.log2n
+    plan = tuple(int(v) for v in a.plan.split(",")) if a.plan else None
+
+    def use_plan(op, dt, key):
+        if plan:
+            api.sincos_plan_set(op, dt, key, *plan)
+
     g = torch.Generator(device="cuda").manual_seed(1)
     x = (torch.rand(n, device="cuda", generator=g) * 2000.0 - 1000.0).contiguous()
     if a.op.startswith("forward"):
@@ -34,6 +42,7 @@ def main(argv=None):
         red = "compensated" if a.op == "forward_compensated" else "plain"
         s = torch.empty(n, dtype=dt, device="cuda")
         c = torch.empty_like(s)
+        use_plan("pairs", dt, n)
         run = lambda: api.sincos_pairs_ex(x, s, c, red)
     elif a.op == "backward":
         gs = torch.randn(n, device="cuda", generator=g)
@@ -42,6 +51,7 @@ def main(argv=None):
         c = torch.empty_like(x)
         api.sincos_pairs(x, s, c)
         gx = torch.empty_like(x)
+        use_plan("backward", "f32", n)
         run = lambda: api.sincos_backward(gs, gc, s, c, gx)
     else:
         # 4096 segments of pseudo-random lengths packed into the n angles
@@ -52,6 +62,7 @@ def main(argv=None):
         s = torch.empty_like(x)
         c = torch.empty_like(x)
         segs, lens_t = api.segments(x, s, c, offs[keep].numpy(), lens[keep].numpy())
+        use_plan("batched", "f32", lens_t.numel())
         run = lambda: api.sincos_batched(segs, lens_t)
     for _ in range(a.launches):
         run()
