@@ -154,6 +154,31 @@ int sincos_batched_ex(const sincos_seg *segs, const int64_t *lens, int count, in
                       int reduction, int coef, sincos_stream_t stream);
 int sincos_batched_release(void);
 
+/* The same batched forward for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is a deployment variant).  A plug-in
+ * inside a host program that owns all device memory, a real-time thread that
+ * must not risk the device-wide synchronization cudaMalloc/cudaFree can
+ * trigger, or code under an allocation budget fixed at start-up cannot let
+ * the library call cudaMalloc for scratch, as sincos_batched does on first
+ * use.  This entry point allocates nothing: its tile-prefix scratch is a
+ * fixed device array of SINCOS_NOALLOC_MAX_SEGMENTS + 1 int64 (512 KiB)
+ * built into the library, present on every GPU that loads it until the
+ * process exits.
+ *   Arguments, layout, results and errors are those of sincos_batched_ex;
+ *   count > SINCOS_NOALLOC_MAX_SEGMENTS returns SINCOS_EUNSUPPORTED before
+ *   anything is enqueued.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before capturing any stream into a graph.
+ *   All calls share the one array: calls whose work can overlap on the GPU
+ *   (different streams without ordering between them) race and give wrong
+ *   results.  Order them on one stream, or use sincos_batched instead.
+ *   Each call rewrites every scratch entry it reads, so the contents left by
+ *   an earlier call do not matter. */
+#define SINCOS_NOALLOC_MAX_SEGMENTS 65536
+int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *lens, int count,
+                           int out_dtype, int reduction, int coef, sincos_stream_t stream);
+
 /* A batched launch captured once into a CUDA graph and replayed.  The graph
  * owns its scratch; the segs/lens device arrays are read at every replay,
  * so their contents (not their addresses) may change between replays. */

@@ -18,6 +18,7 @@ F32, BF16, F16 = 0, 1, 2
 RED_PLAIN, RED_COMPENSATED = 0, 1
 COEF_NORMALIZED, COEF_DAGGER = 0, 1
 OP_PAIRS, OP_BACKWARD, OP_BATCHED = 0, 1, 2
+NOALLOC_MAX_SEGMENTS = 65536
 
 
 class sincos_plan(ctypes.Structure):
@@ -43,6 +44,7 @@ SIGNATURES = {
     "sincos_batched": (_INT, [_VP, _VP, _INT, _VP]),
     "sincos_batched_ex": (_INT, [_VP, _VP, _INT, _INT, _INT, _INT, _VP]),
     "sincos_batched_release": (_INT, []),
+    "sincos_batched_noalloc": (_INT, [_VP, _VP, _INT, _INT, _INT, _INT, _VP]),
     "sincos_batched_graph_create": (_INT, [_VP, _VP, _INT, _INT, _INT, _INT,
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "sincos_batched_graph_launch": (_INT, [_VP, _VP]),

@@ -139,6 +139,22 @@ def sincos_batched(segs: torch.Tensor, lens: torch.Tensor, out_dtype="f32",
               "sincos_batched_ex")
 
 
+def sincos_batched_noalloc(segs: torch.Tensor, lens: torch.Tensor, out_dtype="f32",
+                           reduction: str = "plain", coef: str = "normalized",
+                           stream=None) -> None:
+    """sincos_batched without any device allocation, for callers that must not
+    allocate (its scratch is a fixed array inside the library, shared by all
+    calls; at most ``NOALLOC_MAX_SEGMENTS`` arrays; calls must not overlap on
+    the GPU)."""
+    count = lens.numel()
+    with torch.cuda.device(lens.device):
+        check(lib().sincos_batched_noalloc(_dev(segs, "segs"), _dev(lens, "lens", torch.int64),
+                                           count, _DTYPES[_torch_dtype(out_dtype)],
+                                           _REDUCTIONS[reduction], _COEFS[coef],
+                                           _stream(stream, lens.device)),
+              "sincos_batched_noalloc")
+
+
 def sincos_batched_release() -> None:
     check(lib().sincos_batched_release(), "sincos_batched_release")
 
