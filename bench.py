@@ -40,7 +40,7 @@ WORKLOAD_DESC = ("2^28 float32 angles uniform in [-1000, 1000) (seed 1), float32
                  "outputs (1 GiB in, 2 GiB out), plain reduction, normalized coefficients")
 BYTES_PER_PAIR = 12            # 4 B angle read + 4 B sine + 4 B cosine written
 HBM_FALLBACK_GBS = 6800.0      # only when the measured-peaks file is absent
-FWD_SOURCES = ["core.cuh", "forward.cuh", "forward_f32.cu"]
+FWD_SOURCES = ["core.cuh", "bulk.cuh", "forward.cuh", "forward_f32.cu"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "ncu_forward_f32_bandwidth_2p28.md")
 
 
@@ -518,7 +518,10 @@ def run_ours(args, dist: Dist):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth",
-                         "kernel": "k_forward<float, plain, normalized>",
+                         "kernel": (f"k_forward_bulk<float, plain, normalized, {plan['block']}>"
+                                    if plan["vec_bytes"] == 0 else
+                                    f"k_forward<float, plain, normalized, {plan['unroll']}, "
+                                    f"{plan['vec_bytes']}>"),
                          "bytes_per_launch": BYTES_PER_PAIR * n, "kernel_ms": kernel_ms},
             "errors_vs_fp64": err,
             "cpu_baseline": cpu,

@@ -215,16 +215,23 @@ size_t sincos_host_workspace_bytes(int out_dtype, int64_t chunk_elems);
 
 typedef enum { SINCOS_OP_PAIRS = 0, SINCOS_OP_BACKWARD = 1, SINCOS_OP_BATCHED = 2 } sincos_op;
 
-/* A launch configuration: threads per CTA, output vectors each thread
- * keeps in flight per iteration, resident CTAs per SM that the grid is sized
- * for, and the bytes of output one thread writes per vector and per array
- * (16: st.v4; 32: 256-bit st.v8).  A vector holds vec_bytes / sizeof(out)
- * pairs, and a batched tile is block * unroll of them. */
+/* A launch configuration.
+ * Register path (vec_bytes 16 or 32): threads per CTA, output vectors each
+ * thread keeps in flight per iteration, resident CTAs per SM that the grid
+ * is sized for, and the bytes of output one thread writes per vector and per
+ * array (16: st.v4; 32: 256-bit st.v8).  A vector holds vec_bytes /
+ * sizeof(out) pairs; a batched tile is block * unroll of them.
+ * Bulk path (vec_bytes 0, single-array forward only): TMA bulk copies stage
+ * 8192-angle chunks through a two-stage shared-memory ring and bulk stores
+ * write the results (about 192 KB of shared memory, one CTA per SM); block
+ * is 128, 256, 512 or 1024 and unroll / ctas_per_sm are not used.  Arrays
+ * shorter than one chunk, and the backward and batched kernels, fall back to
+ * the 16-byte register path. */
 typedef struct {
     int block;        /* 64 .. 1024, multiple of 32 */
     int unroll;       /* 1, 2, 4 or 8 */
     int ctas_per_sm;  /* 1 .. 32 */
-    int vec_bytes;    /* 16 or 32; 0 selects 32 */
+    int vec_bytes;    /* 16 or 32 (register path) or 0 (bulk path) */
 } sincos_plan;
 
 /* The plan used for (op, out_dtype, n) on the current device: the tuned one
@@ -262,6 +269,11 @@ int sincos_plan_cache_load(const char *path);
 const char *sincos_strerror(int status);
 /* Text of the last failed CUDA call on this host thread ("" if none). */
 const char *sincos_last_error(void);
+/* Bounded waits inside bulk-path kernels that gave up (an mbarrier that did
+ * not complete within its iteration limit) on the current device since the
+ * previous call; the count is cleared by reading it.  Nonzero means a launch
+ * stopped early and its outputs are incomplete.  Synchronizes the device. */
+uint32_t sincos_device_wait_timeouts(void);
 /* Kernel launches this library has enqueued since load (all threads); a
  * graph replay counts the kernels in the graph. */
 uint64_t sincos_launch_count(void);

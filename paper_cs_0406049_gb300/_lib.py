@@ -27,7 +27,7 @@ class sincos_plan(ctypes.Structure):
 
     def as_dict(self):
         return {"block": self.block, "unroll": self.unroll, "ctas_per_sm": self.ctas_per_sm,
-                "vec_bytes": self.vec_bytes if self.vec_bytes else 32}
+                "vec_bytes": self.vec_bytes}
 
 
 class sincos_seg(ctypes.Structure):
@@ -60,6 +60,7 @@ SIGNATURES = {
     "sincos_plan_cache_load": (_INT, [ctypes.c_char_p]),
     "sincos_strerror": (ctypes.c_char_p, [_INT]),
     "sincos_last_error": (ctypes.c_char_p, []),
+    "sincos_device_wait_timeouts": (ctypes.c_uint32, []),
     "sincos_launch_count": (ctypes.c_uint64, []),
     "sincos_version": (_INT, []),
 }

@@ -276,6 +276,11 @@ def sincos_plan_cache_load(path: str) -> None:
     check(lib().sincos_plan_cache_load(path.encode()), "sincos_plan_cache_load")
 
 
+def sincos_device_wait_timeouts() -> int:
+    """Bounded waits that gave up in bulk-path kernels since the last call."""
+    return int(lib().sincos_device_wait_timeouts())
+
+
 def sincos_launch_count() -> int:
     return int(lib().sincos_launch_count())
 

@@ -99,6 +99,29 @@ int resident_ctas(const void *kernel, int block, int want)
     return per_sm < want ? per_sm : want;
 }
 
+int bulk_resident_ctas(const void *kernel, int block, size_t smem)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t key = ((uint64_t)(uintptr_t)kernel << 16) ^ ((uint64_t)block << 6) ^
+                         (uint64_t)dev ^ 0x5bd1e995ull;
+    {
+        std::lock_guard<std::mutex> lock(g_occ_mu);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) return it->second;
+    }
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    g_occ[key] = per_sm;
+    return per_sm;
+}
+
 sincos_plan fit_plan(const void *kernel, const sincos_plan &plan, int *per_sm)
 {
     sincos_plan p = plan;
@@ -183,6 +206,11 @@ const char *sincos_strerror(int status)
 }
 
 const char *sincos_last_error(void) { return g_last_error.c_str(); }
+
+uint32_t sincos_device_wait_timeouts(void)
+{
+    return take_timeouts_forward_f32() + take_timeouts_forward_bf16() + take_timeouts_forward_f16();
+}
 
 uint64_t sincos_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -162,7 +162,7 @@ static int launch_bwd_gc(const float *gs, const float *gc, const float *s, const
     if (GS) { ptrs[k++] = gs; ptrs[k++] = c; }
     if (GC) { ptrs[k++] = gc; ptrs[k++] = s; }
     ptrs[k++] = gx;
-    if (plan_vec_bytes(plan) == 32) {
+    if (reg_vec_bytes(plan) == 32) {
         const int h = backward_head(ptrs, k, 32);
         if (h >= 0) return launch_bwd_w<GS, GC, 32>(gs, gc, s, c, gx, n, h, in_place, plan, dev, st);
     }

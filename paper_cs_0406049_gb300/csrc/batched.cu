@@ -200,7 +200,7 @@ __global__ void k_batched(const sincos_seg *segs, const int64_t *lens, const int
 
 int64_t batched_tile_elems(const sincos_plan &plan, int dtype)
 {
-    return (int64_t)plan.block * plan.unroll * (plan_vec_bytes(plan) / dtype_size(dtype));
+    return (int64_t)plan.block * plan.unroll * (reg_vec_bytes(plan) / dtype_size(dtype));
 }
 
 template <class OutT, int RED, int COEF, int W>
@@ -218,7 +218,7 @@ static const void *tiles_kernel_w(int unroll)
 template <class OutT, int RED, int COEF>
 static const void *tiles_kernel_rc(const sincos_plan &plan)
 {
-    if (plan_vec_bytes(plan) == 32) return tiles_kernel_w<OutT, RED, COEF, 32>(plan.unroll);
+    if (reg_vec_bytes(plan) == 32) return tiles_kernel_w<OutT, RED, COEF, 32>(plan.unroll);
     return tiles_kernel_w<OutT, RED, COEF, 16>(plan.unroll);
 }
 
@@ -247,7 +247,7 @@ int launch_batched(const sincos_seg *segs, const int64_t *lens, int count, int d
     const sincos_plan p = fit_plan(fn, plan, &per_sm);
     if (per_sm <= 0) return SINCOS_EUNSUPPORTED;
     const int64_t tile = batched_tile_elems(p, dtype);
-    const bool w32 = plan_vec_bytes(p) == 32;
+    const bool w32 = reg_vec_bytes(p) == 32;
     if (dtype == SINCOS_F32)
         (w32 ? k_batched_prefix<float, 32> : k_batched_prefix<float, 16>)
             <<<1, 1024, 0, st>>>(segs, lens, count, tile, prefix);

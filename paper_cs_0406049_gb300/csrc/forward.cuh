@@ -16,6 +16,7 @@
 // common vector alignment take the element-wise kernel.
 #pragma once
 
+#include "bulk.cuh"
 #include "core.cuh"
 #include "internal.h"
 
@@ -109,6 +110,19 @@ template <class OutT, int RED, int COEF>
 static int launch_forward_rc(const float *x, OutT *s, OutT *c, int64_t n, bool in_place,
                              const sincos_plan &plan, const DeviceInfo &dev, cudaStream_t st)
 {
+    // Bulk (TMA-staged) path when the plan asks for it and the array holds at
+    // least one whole chunk after its aligned start.
+    if (plan_vec_bytes(plan) == 0) {
+        const int h = vector_head<OutT, 16>(x, s, c);
+        if (h >= 0 && n - h >= kBulkChunk) {
+            switch (plan.block) {
+            case 128: return launch_forward_bulk_nt<OutT, RED, COEF, 128>(x, s, c, n, h, dev, st);
+            case 512: return launch_forward_bulk_nt<OutT, RED, COEF, 512>(x, s, c, n, h, dev, st);
+            case 1024: return launch_forward_bulk_nt<OutT, RED, COEF, 1024>(x, s, c, n, h, dev, st);
+            default: return launch_forward_bulk_nt<OutT, RED, COEF, 256>(x, s, c, n, h, dev, st);
+            }
+        }
+    }
     // The plan's access width first; a 16-byte vector path if the pointers
     // only admit that; element-wise otherwise.
     if (plan_vec_bytes(plan) == 32) {

@@ -11,4 +11,6 @@ int launch_forward_bf16(const float *x, void *s, void *c, int64_t n, int red, in
                                            false, plan, dev, st);
 }
 
+unsigned take_timeouts_forward_bf16() { return take_bulk_wait_timeouts_here(); }
+
 }  // namespace sincos_gb300

@@ -19,4 +19,6 @@ int launch_forward(const float *x, void *s, void *c, int64_t n, int dtype, int r
     return launch_forward_f16(x, s, c, n, red, coef, plan, dev, st);
 }
 
+unsigned take_timeouts_forward_f32() { return take_bulk_wait_timeouts_here(); }
+
 }  // namespace sincos_gb300

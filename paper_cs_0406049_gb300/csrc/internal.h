@@ -45,8 +45,19 @@ inline int dtype_size(int d) { return d == SINCOS_F32 ? 4 : 2; }
 // Plan lookup (tuned or default) for the current device.
 sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n);
 bool plan_valid(const sincos_plan &p);
-// Bytes each thread moves per output vector (16 or 32); 0 in a plan means 32.
-inline int plan_vec_bytes(const sincos_plan &p) { return p.vec_bytes == 16 ? 16 : 32; }
+// The plan's forward path: 0 = bulk (TMA-staged) kernel, 16 or 32 = register
+// path with that many bytes per thread per output vector.
+inline int plan_vec_bytes(const sincos_plan &p) { return p.vec_bytes == 0 ? 0 : p.vec_bytes == 16 ? 16 : 32; }
+// The register-path width for kernels without a bulk variant.
+inline int reg_vec_bytes(const sincos_plan &p) { return p.vec_bytes == 32 ? 32 : 16; }
+// Opt a kernel into `smem` bytes of dynamic shared memory (once per kernel and
+// device) and return its resident CTAs per SM at that size.
+int bulk_resident_ctas(const void *kernel, int block, size_t smem);
+// Bounded waits that gave up in bulk kernels, per translation unit (each
+// read clears the count).
+unsigned take_timeouts_forward_f32();
+unsigned take_timeouts_forward_bf16();
+unsigned take_timeouts_forward_f16();
 
 // Kernel launchers.  Arguments are already validated; they enqueue on `st`
 // and return a status.

@@ -2,7 +2,7 @@
 // a JSON file) and the autotuner that fills it.
 //
 // A plan is (threads per CTA, vectors in flight per thread, resident CTAs per
-// SM, bytes per vector access).  Plans are keyed by device ("<name>:<SMs>"), operation,
+// SM, bytes per vector access -- or 0 for the bulk-copy path).  Plans are keyed by device ("<name>:<SMs>"), operation,
 // output dtype and the bit length of the element count, so one tuning run
 // per size class covers every later call in that class.
 #include <algorithm>
@@ -47,10 +47,12 @@ sincos_plan default_plan(int op, int dtype)
     // Fastest plans of a GB300 sweep (2^26..2^28 elements, 4096-array batch).
     // About 1024 resident threads per SM with 2..8 vectors in flight each
     // beat full occupancy: fewer concurrent streams keep DRAM pages open.
+    // The binary32 single-array forward defaults to the bulk (TMA-staged)
+    // path; 16-bit outputs run faster on the 32-byte register path.
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
-    if (dtype != SINCOS_F32) return sincos_plan{256, 2, 4, 32};
-    if (op == SINCOS_OP_BATCHED) return sincos_plan{1024, 2, 1, 16};
-    return sincos_plan{256, 8, 4, 16};
+    if (op == SINCOS_OP_BATCHED)
+        return dtype == SINCOS_F32 ? sincos_plan{1024, 2, 1, 16} : sincos_plan{256, 2, 4, 32};
+    return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
 }
 
 int load_file(const char *path);
@@ -149,9 +151,11 @@ void store_plan(const DeviceInfo &dev, int op, int dtype, int64_t n, const sinco
     g_plans[PlanKey(device_key(dev), op, dtype, bucket_of(n))] = p;
 }
 
-std::vector<sincos_plan> candidates(const DeviceInfo &dev)
+std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
 {
     std::vector<sincos_plan> out;
+    if (op == SINCOS_OP_PAIRS)      // bulk path: one CTA per SM, CTA size only
+        for (int block : {128, 256, 512, 1024}) out.push_back(sincos_plan{block, 2, 1, 0});
     const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
     for (int vec : {16, 32})
         for (int block : {128, 256, 512, 1024})
@@ -213,7 +217,7 @@ int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F
     if (stream_is_capturing(st)) return SINCOS_ECAPTURE;
     float best_ms = -1.f;
     sincos_plan best_plan = default_plan(op, dtype);
-    for (const sincos_plan &p : candidates(dev)) {
+    for (const sincos_plan &p : candidates(dev, op)) {
         const float ms = time_plan([&] { return launch_with(p); }, st, 3);
         if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
             best_ms = ms;
@@ -233,7 +237,9 @@ bool plan_valid(const sincos_plan &p)
     return p.block >= 64 && p.block <= 1024 && p.block % 32 == 0 &&
            (p.unroll == 1 || p.unroll == 2 || p.unroll == 4 || p.unroll == 8) &&
            p.ctas_per_sm >= 1 && p.ctas_per_sm <= 32 &&
-           (p.vec_bytes == 0 || p.vec_bytes == 16 || p.vec_bytes == 32);
+           (p.vec_bytes == 0 || p.vec_bytes == 16 || p.vec_bytes == 32) &&
+           (p.vec_bytes != 0 || p.block == 128 || p.block == 256 || p.block == 512 ||
+            p.block == 1024);
 }
 
 sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n)

@@ -68,3 +68,24 @@ def mixed_angles(n: int, seed: int) -> np.ndarray:
     k = min(sp.size, n)
     x[rng.choice(n, k, replace=False)] = sp[:k]
     return x
+
+
+class forced_plan:
+    """Use one launch plan for every size class of (op, dtype) inside a with
+    block, restoring the previous plans afterwards."""
+
+    def __init__(self, op: str, dtype: str, plan):
+        self.op, self.dtype, self.plan = op, dtype, tuple(plan)
+
+    def __enter__(self):
+        from paper_cs_0406049_gb300 import api
+        self.saved = [(b, api.sincos_plan_get(self.op, self.dtype, 1 << b)) for b in range(0, 41)]
+        for b, _ in self.saved:
+            api.sincos_plan_set(self.op, self.dtype, 1 << b, *self.plan)
+        return self
+
+    def __exit__(self, *exc):
+        from paper_cs_0406049_gb300 import api
+        for b, p in self.saved:
+            api.sincos_plan_set(self.op, self.dtype, 1 << b, p["block"], p["unroll"],
+                                p["ctas_per_sm"], p["vec_bytes"])

@@ -113,7 +113,9 @@ def test_plan_validation(lib):
     assert lib.sincos_plan_set(0, 0, 1 << 20, ctypes.byref(bad)) == _lib.EINVAL
     bad = _lib.sincos_plan(256, 3, 8, 0)       # unroll not 1/2/4/8
     assert lib.sincos_plan_set(0, 0, 1 << 20, ctypes.byref(bad)) == _lib.EINVAL
-    bad = _lib.sincos_plan(256, 4, 8, 64)      # vector width not 16/32
+    bad = _lib.sincos_plan(96, 2, 1, 0)        # bulk path needs 128/256/512/1024 threads
+    assert lib.sincos_plan_set(0, 0, 1 << 20, ctypes.byref(bad)) == _lib.EINVAL
+    bad = _lib.sincos_plan(256, 4, 8, 64)      # vector width not 0/16/32
     assert lib.sincos_plan_set(0, 0, 1 << 20, ctypes.byref(bad)) == _lib.EINVAL
     good = _lib.sincos_plan(256, 4, 8, 0)
     assert lib.sincos_plan_set(9, 0, 1 << 20, ctypes.byref(good)) == _lib.EINVAL

@@ -11,7 +11,7 @@ import torch
 
 import oracle
 from gpu_util import (PARITY_ABS_TOL, as_np, assert_16_parity, assert_f32_parity,
-                      mixed_angles, special_angles)
+                      forced_plan, mixed_angles, special_angles)
 from paper_cs_0406049_gb300 import api, workloads
 
 pytestmark = pytest.mark.gpu
@@ -72,25 +72,54 @@ def run_guarded(x, dtype, red, coef, offs):
     return as_np(ss), as_np(cs)
 
 
+# Element offsets (x, s, c) into guard-padded buffers.  Equal offsets share a
+# 128-byte line grid (line-aligned vector path after a scalar head); (0, 1, 2),
+# (3, 0, 1) in f32 still share a 16-byte grid for some heads or none; for
+# 16-bit outputs (1, 5, 5), (2, 4, 4) and (0, 1, 3) admit no common vector
+# alignment (element-wise path).
 OFFSETS = {
     "f32": [(0, 0, 0), (1, 1, 1), (2, 2, 2), (3, 3, 3), (0, 1, 2), (3, 0, 1)],
-    # (1, 5, 5): vector path after a head of 3; (2, 4, 4) and (0, 1, 3): no
-    # common 16-byte alignment, element-wise path
-    "bf16": [(0, 0, 0), (1, 5, 5), (2, 4, 4), (0, 1, 3)],
-    "f16": [(0, 0, 0), (1, 5, 5), (2, 4, 4), (0, 1, 3)],
+    "bf16": [(0, 0, 0), (1, 1, 1), (3, 3, 3), (1, 5, 5), (2, 4, 4), (0, 1, 3)],
+    "f16": [(0, 0, 0), (1, 1, 1), (3, 3, 3), (1, 5, 5), (2, 4, 4), (0, 1, 3)],
 }
 
 
+PATHS = {"bulk": (512, 2, 1, 0), "reg16": (256, 8, 4, 16), "reg32": (256, 4, 4, 32)}
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("dtype,red,coef", VARIANTS)
-def test_ragged_sizes_and_alignments(cuda_lib, dtype, red, coef):
-    for n in SIZES:
-        x = mixed_angles(n, seed=n)
-        want_s, want_c = oracle_out(x, dtype, red, coef)
-        for offs in OFFSETS[dtype]:
-            if n > 70000 and offs != (0, 0, 0) and offs != OFFSETS[dtype][1]:
-                continue
-            s, c = run_guarded(x, dtype, red, coef, offs)
-            check(dtype, s, c, want_s, want_c, f"{dtype}/{red}/{coef} n={n} offs={offs}")
+def test_ragged_sizes_and_alignments(cuda_lib, dtype, red, coef, path):
+    with forced_plan("pairs", dtype, PATHS[path]):
+        for n in SIZES:
+            x = mixed_angles(n, seed=n)
+            want_s, want_c = oracle_out(x, dtype, red, coef)
+            for offs in OFFSETS[dtype]:
+                if n > 70000 and offs != (0, 0, 0) and offs != OFFSETS[dtype][1]:
+                    continue
+                s, c = run_guarded(x, dtype, red, coef, offs)
+                check(dtype, s, c, want_s, want_c,
+                      f"{path} {dtype}/{red}/{coef} n={n} offs={offs}")
+    assert api.sincos_device_wait_timeouts() == 0
+
+
+BULK_SIZES = [8191, 8192, 8193, 8192 + 31, 8192 + 33, 2 * 8192, 3 * 8192 + 5, 152 * 8192,
+              152 * 8192 + 8191, 153 * 8192 - 1, 1000 * 8192 + 4099]
+
+
+@pytest.mark.parametrize("block", [128, 256, 512, 1024])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_bulk_path_chunk_boundaries(cuda_lib, dtype, block):
+    """Whole chunks, partial tails and heads around the 8192-angle chunk and
+    the 152-CTA grid, on line-aligned and offset pointers."""
+    with forced_plan("pairs", dtype, (block, 2, 1, 0)):
+        for n in BULK_SIZES:
+            x = mixed_angles(n, seed=n + block)
+            want_s, want_c = oracle_out(x, dtype, "plain", "normalized")
+            for offs in OFFSETS[dtype][:2]:
+                s, c = run_guarded(x, dtype, "plain", "normalized", offs)
+                check(dtype, s, c, want_s, want_c, f"bulk{block} {dtype} n={n} offs={offs}")
+    assert api.sincos_device_wait_timeouts() == 0
 
 
 def test_plain_entry_point_on_the_plain_workload(cuda_lib):
@@ -131,7 +160,13 @@ def test_every_float_in_a_binade(cuda_lib):
         assert_f32_parity(as_np(c), want_c, red + " c")
 
 
-def test_in_place(cuda_lib):
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_in_place(cuda_lib, path):
+    with forced_plan("pairs", "f32", PATHS[path]):
+        _in_place()
+
+
+def _in_place():
     x = mixed_angles(100003, seed=5)
     want_s, want_c = oracle.sincos(x)
     buf = torch.from_numpy(x.copy()).cuda()

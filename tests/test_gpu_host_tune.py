@@ -64,7 +64,8 @@ def test_autotune_pairs_and_plan_cache(cuda_lib, tmp_path):
 
 
 @pytest.mark.parametrize("plan", [(64, 1, 1, 16), (128, 8, 16, 32), (1024, 8, 2, 32),
-                                  (96, 2, 3, 16), (256, 4, 4, 32)])
+                                  (96, 2, 3, 16), (256, 4, 4, 32), (128, 2, 1, 0),
+                                  (1024, 2, 1, 0)])
 def test_every_plan_shape_is_exact(cuda_lib, plan):
     """Odd plans (small grids, big unrolls, non-power-of-two blocks) change
     only the schedule, never the results."""
