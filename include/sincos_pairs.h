@@ -140,8 +140,8 @@ typedef struct {
  *   lens  device array of `count` int64 lengths; a negative length counts
  *         as 0.  Both arrays are read when the kernels run, so they may be
  *         filled by earlier work on the same stream.
- * Outputs of different segments must not overlap (not checked: the
- * descriptors live on the device).
+ * No output may overlap another segment's output or any segment's angles
+ * (not checked: the descriptors live on the device).
  * Scratch: the library keeps one small device buffer ((count+1) int64) per
  * (device, stream) pair, allocated with cudaMalloc on the first call that
  * needs a larger one.  A call that would allocate while `stream` is being
@@ -221,12 +221,12 @@ typedef enum { SINCOS_OP_PAIRS = 0, SINCOS_OP_BACKWARD = 1, SINCOS_OP_BATCHED = 
  * is sized for, and the bytes of output one thread writes per vector and per
  * array (16: st.v4; 32: 256-bit st.v8).  A vector holds vec_bytes /
  * sizeof(out) pairs; a batched tile is block * unroll of them.
- * Bulk path (vec_bytes 0, single-array forward only): TMA bulk copies stage
- * 8192-angle chunks through a two-stage shared-memory ring and bulk stores
- * write the results (about 192 KB of shared memory, one CTA per SM); block
- * is 128, 256, 512 or 1024 and unroll / ctas_per_sm are not used.  Arrays
- * shorter than one chunk, and the backward and batched kernels, fall back to
- * the 16-byte register path. */
+ * Bulk path (vec_bytes 0; forward and batched): TMA bulk copies stage
+ * 8192-angle chunks (batched: tiles) through a two-stage shared-memory ring
+ * and bulk stores write the results (up to 192 KB of shared memory, one CTA
+ * per SM); block is 128, 256, 512 or 1024 and unroll / ctas_per_sm are not
+ * used.  Single arrays shorter than one chunk, and the backward kernel, use
+ * the 16-byte register path instead. */
 typedef struct {
     int block;        /* 64 .. 1024, multiple of 32 */
     int unroll;       /* 1, 2, 4 or 8 */

@@ -78,7 +78,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}{r.stderr}")
         return obj, r.stderr
 
-    srcs = _sources()
+    # longest translation units first, so the pool finishes evenly
+    srcs = sorted(_sources(), key=lambda f: -os.path.getsize(f) -
+                  (1 << 20 if os.path.basename(f).startswith(("batched_", "forward_")) else 0))
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         results = list(ex.map(compile_one, srcs))
     if verbose or ptxas_verbose:

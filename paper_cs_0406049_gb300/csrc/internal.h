@@ -58,6 +58,9 @@ int bulk_resident_ctas(const void *kernel, int block, size_t smem);
 unsigned take_timeouts_forward_f32();
 unsigned take_timeouts_forward_bf16();
 unsigned take_timeouts_forward_f16();
+unsigned take_timeouts_batched_f32();
+unsigned take_timeouts_batched_bf16();
+unsigned take_timeouts_batched_f16();
 
 // Kernel launchers.  Arguments are already validated; they enqueue on `st`
 // and return a status.
@@ -73,7 +76,5 @@ int launch_batched(const sincos_seg *segs, const int64_t *lens, int count, int d
                    int coef, int64_t *prefix, const sincos_plan &plan, const DeviceInfo &dev,
                    cudaStream_t st);
 
-// Elements per batched tile for a plan and output dtype.
-int64_t batched_tile_elems(const sincos_plan &plan, int dtype);
 
 }  // namespace sincos_gb300

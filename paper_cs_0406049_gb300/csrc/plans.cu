@@ -51,7 +51,7 @@ sincos_plan default_plan(int op, int dtype)
     // path; 16-bit outputs run faster on the 32-byte register path.
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
     if (op == SINCOS_OP_BATCHED)
-        return dtype == SINCOS_F32 ? sincos_plan{1024, 2, 1, 16} : sincos_plan{256, 2, 4, 32};
+        return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
     return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
 }
 
@@ -154,7 +154,7 @@ void store_plan(const DeviceInfo &dev, int op, int dtype, int64_t n, const sinco
 std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
 {
     std::vector<sincos_plan> out;
-    if (op == SINCOS_OP_PAIRS)      // bulk path: one CTA per SM, CTA size only
+    if (op != SINCOS_OP_BACKWARD)   // bulk path: one CTA per SM, CTA size only
         for (int block : {128, 256, 512, 1024}) out.push_back(sincos_plan{block, 2, 1, 0});
     const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
     for (int vec : {16, 32})

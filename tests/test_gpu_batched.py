@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import as_np, assert_16_parity, assert_f32_parity, mixed_angles
+from gpu_util import as_np, assert_16_parity, assert_f32_parity, forced_plan, mixed_angles
 from paper_cs_0406049_gb300 import api, workloads
 
 pytestmark = pytest.mark.gpu
@@ -35,27 +35,36 @@ def check_all(x, s, c, dtype, red, coef, what):
         assert_16_parity(as_np(c), want_c, dtype == "bf16", what + " c")
 
 
-EDGE_LENS = [1, 0, 3, 4095, 4096, 4097, 8191, 2, 65536 + 17, 5, 0, 0, 1, 1 << 20, 31, 7, 8]
+EDGE_LENS = [1, 0, 3, 4095, 4096, 4097, 8191, 8192, 8193, 2, 65536 + 17, 5, 0, 0, 1, 1 << 20,
+             31, 7, 8, 3 * 8192 + 63, 64, 65]
+PATHS = {"bulk256": (256, 2, 1, 0), "bulk1024": (1024, 2, 1, 0), "reg16": (1024, 2, 1, 16),
+         "reg32": (256, 4, 8, 32)}
 
 
+@pytest.mark.parametrize("path", sorted(PATHS))
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("red,coef", [("plain", "normalized"), ("compensated", "dagger")])
-def test_edge_lengths(cuda_lib, dtype, red, coef):
+def test_edge_lengths(cuda_lib, dtype, red, coef, path):
     x, xt, s, c, offs = packed(EDGE_LENS, dtype, seed=1)
     segs, lens = api.segments(xt, s, c, offs, EDGE_LENS)
-    api.sincos_batched(segs, lens, dtype, red, coef)
-    check_all(x, s, c, dtype, red, coef, f"batched {dtype}")
+    with forced_plan("batched", dtype, PATHS[path]):
+        api.sincos_batched(segs, lens, dtype, red, coef)
+    check_all(x, s, c, dtype, red, coef, f"batched {path} {dtype}")
+    assert api.sincos_device_wait_timeouts() == 0
 
 
-def test_negative_and_empty_lengths(cuda_lib):
-    lens = [5, -3, 0, 9, -100, 1]
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_negative_and_empty_lengths(cuda_lib, path):
+    lens = [5, -3, 0, 9, -100, 1, 20000, -1]
     x, xt, s, c, offs = packed(lens, "f32", seed=2)
     segs, lens_t = api.segments(xt, s, c, offs, lens)
-    api.sincos_batched(segs, lens_t)
+    with forced_plan("batched", "f32", PATHS[path]):
+        api.sincos_batched(segs, lens_t)
     check_all(x, s, c, "f32", "plain", "normalized", "negative lengths")
 
 
-def test_separate_tensors_mixed_alignment(cuda_lib):
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_separate_tensors_mixed_alignment(cuda_lib, path):
     """Segments as separate tensors whose x, s and c start at different
     offsets modulo 16 bytes (the element-wise path inside tiles)."""
     rng = np.random.default_rng(4)
@@ -73,7 +82,8 @@ def test_separate_tensors_mixed_alignment(cuda_lib):
         xn.append(a)
         keep += [bx, bs, bc]
     segs, lens = api.segments_from_lists(xs, ss, cs)
-    api.sincos_batched(segs, lens)
+    with forced_plan("batched", "f32", PATHS[path]):
+        api.sincos_batched(segs, lens)
     torch.cuda.synchronize()
     for i, a in enumerate(xn):
         want_s, want_c = oracle.sincos(a)
