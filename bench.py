@@ -200,6 +200,12 @@ def profiled_traffic():
     return float(m.group(1))
 
 
+def aggregate_value(world: int, n_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job pairs/s: every rank computed n_per_rank pairs per step; the
+    slowest rank's time for all steps bounds the job."""
+    return world * n_per_rank * steps / (max_ms * 1e-3)
+
+
 def fp64_errors(x: np.ndarray, s: np.ndarray, c: np.ndarray) -> dict:
     """Max abs error of binary32 results against FP64 sin/cos of the same
     angles, also in units of ulp(1.0) = 2^-23, and the largest per-result ulp
@@ -457,7 +463,7 @@ def run_ours(args, dist: Dist):
     if sampler:
         sampler.stop()
     max_ms = dist.max(total_ms)
-    value = dist.world * n * args.steps / (max_ms * 1e-3)
+    value = aggregate_value(dist.world, n, args.steps, max_ms)
     kernel_ms = statistics.mean(per)
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_PAIR * n / (kernel_ms * 1e-3) / 1e9
