@@ -103,6 +103,19 @@ int sincos_pairs(const float *x, float *s, float *c, int64_t n, sincos_stream_t 
 int sincos_pairs_ex(const float *x, void *s, void *c, int64_t n, int out_dtype,
                     int reduction, int coef, sincos_stream_t stream);
 
+/* exp(i x) = cos x + i sin x for 0 <= i < n as interleaved complex64:
+ * z[2i] = c_i, z[2i+1] = s_i, the same pairs as sincos_pairs_ex with
+ * SINCOS_F32 output (Sec. Methodology; the pair of the paper's struct
+ * phase, written as one complex stream for FFT and phase-factor consumers).
+ *   x  device, n floats, read only.
+ *   z  device, 2n floats, written; must not overlap x.  Any 4-byte
+ *      alignment works; the vector paths need z + 2h and x + h to share a
+ *      16-byte grid for some small h (always true for complex64 storage and
+ *      16-byte aligned x).
+ * Uses the SINCOS_OP_PAIRS / SINCOS_F32 launch plan (bulk or register path). */
+int sincos_expi(const float *x, float *z, int64_t n, int reduction, int coef,
+                sincos_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Backward                                                                  */
 /* ------------------------------------------------------------------------ */

@@ -40,6 +40,7 @@ _PLANP = ctypes.POINTER(sincos_plan)
 SIGNATURES = {
     "sincos_pairs": (_INT, [_VP, _VP, _VP, _I64, _VP]),
     "sincos_pairs_ex": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP]),
+    "sincos_expi": (_INT, [_VP, _VP, _I64, _INT, _INT, _VP]),
     "sincos_backward": (_INT, [_VP, _VP, _VP, _VP, _VP, _I64, _VP]),
     "sincos_batched": (_INT, [_VP, _VP, _INT, _VP]),
     "sincos_batched_ex": (_INT, [_VP, _VP, _INT, _INT, _INT, _INT, _VP]),

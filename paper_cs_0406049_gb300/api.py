@@ -85,6 +85,27 @@ def sincos_pairs_ex(x: torch.Tensor, s: torch.Tensor, c: torch.Tensor, reduction
               "sincos_pairs_ex")
 
 
+def sincos_expi(x: torch.Tensor, z: torch.Tensor, reduction: str = "plain",
+                coef: str = "normalized", stream=None) -> None:
+    """z = exp(i x) as interleaved (cos, sin): a complex64 tensor of x's size
+    or a float32 tensor of twice its size."""
+    n = x.numel()
+    zf = torch.view_as_real(z) if z.is_complex() else z
+    if zf.dtype != torch.float32 or zf.numel() != 2 * n:
+        raise ValueError("z must be complex64 with x's size, or float32 with twice it")
+    with torch.cuda.device(x.device):
+        check(lib().sincos_expi(_dev(x, "x", torch.float32), _dev(zf, "z"), n,
+                                _REDUCTIONS[reduction], _COEFS[coef], _stream(stream, x.device)),
+              "sincos_expi")
+
+
+def expi(x: torch.Tensor, reduction: str = "plain", coef: str = "normalized") -> torch.Tensor:
+    """exp(i x) as a new complex64 tensor shaped like x."""
+    z = torch.empty(x.shape, dtype=torch.complex64, device=x.device)
+    sincos_expi(x.contiguous(), z, reduction, coef)
+    return z
+
+
 def sincos_backward(gs, gc, s: torch.Tensor, c: torch.Tensor, gx: torch.Tensor,
                     stream=None) -> None:
     """gx = gs*c - gc*s; gs or gc may be None (an all-zero upstream gradient)."""

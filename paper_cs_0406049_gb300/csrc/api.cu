@@ -210,7 +210,8 @@ const char *sincos_last_error(void) { return g_last_error.c_str(); }
 uint32_t sincos_device_wait_timeouts(void)
 {
     return take_timeouts_forward_f32() + take_timeouts_forward_bf16() + take_timeouts_forward_f16() +
-           take_timeouts_batched_f32() + take_timeouts_batched_bf16() + take_timeouts_batched_f16();
+           take_timeouts_batched_f32() + take_timeouts_batched_bf16() + take_timeouts_batched_f16() +
+           take_timeouts_expi();
 }
 
 uint64_t sincos_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

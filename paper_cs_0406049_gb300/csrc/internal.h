@@ -61,6 +61,7 @@ unsigned take_timeouts_forward_f16();
 unsigned take_timeouts_batched_f32();
 unsigned take_timeouts_batched_bf16();
 unsigned take_timeouts_batched_f16();
+unsigned take_timeouts_expi();
 
 // Kernel launchers.  Arguments are already validated; they enqueue on `st`
 // and return a status.

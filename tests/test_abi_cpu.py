@@ -70,6 +70,15 @@ def test_forward_validation(lib, args, status):
     assert lib.sincos_pairs_ex(*args) == status
 
 
+def test_expi_validation(lib):
+    assert lib.sincos_expi(A, A + 4096, -1, 0, 0, None) == _lib.EINVAL
+    assert lib.sincos_expi(None, A + 4096, 8, 0, 0, None) == _lib.EINVAL
+    assert lib.sincos_expi(A, A + 4096, 8, 5, 0, None) == _lib.EINVAL
+    assert lib.sincos_expi(A, A + 16, 8, 0, 0, None) == _lib.EOVERLAP      # z overlaps x
+    assert lib.sincos_expi(A, A, 8, 0, 0, None) == _lib.EOVERLAP           # no in-place
+    assert lib.sincos_expi(None, None, 0, 0, 0, None) == _lib.OK
+
+
 def test_plain_forward_validation(lib):
     assert lib.sincos_pairs(A, A + 4096, A + 8192, -5, None) == _lib.EINVAL
     assert lib.sincos_pairs(A, A + 4096, A + 4096, 8, None) == _lib.EOVERLAP
