@@ -353,10 +353,13 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
 
     # exp(i x) as interleaved complex64 on the same angles: 12 B per angle
     z = torch.empty(x.size, dtype=torch.complex64, device="cuda")
+    if autotune:
+        api.sincos_autotune_expi(xt, z)
     total, per, _ = time_loop(torch, lambda: api.sincos_expi(xt, z), k, 3, dist)
     ms = statistics.mean(per)
     out["expi_complex64_2p26"] = {"gbs": 12 * x.size / (ms * 1e-3) / 1e9, "ms": ms,
-                                  "frac_of_peak": 12 * x.size / (ms * 1e-3) / 1e9 / peak}
+                                  "frac_of_peak": 12 * x.size / (ms * 1e-3) / 1e9 / peak,
+                                  "plan": api.sincos_plan_get("expi", "f32", x.size)}
     del z, xt
 
     # backward: 2^26 angles U[-50, 50), gs, gc ~ N(0, 1): 20 B per element

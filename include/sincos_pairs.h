@@ -112,7 +112,7 @@ int sincos_pairs_ex(const float *x, void *s, void *c, int64_t n, int out_dtype,
  *      alignment works; the vector paths need z + 2h and x + h to share a
  *      16-byte grid for some small h (always true for complex64 storage and
  *      16-byte aligned x).
- * Uses the SINCOS_OP_PAIRS / SINCOS_F32 launch plan (bulk or register path). */
+ * Uses the SINCOS_OP_EXPI launch plan (bulk or register path). */
 int sincos_expi(const float *x, float *z, int64_t n, int reduction, int coef,
                 sincos_stream_t stream);
 
@@ -226,7 +226,12 @@ size_t sincos_host_workspace_bytes(int out_dtype, int64_t chunk_elems);
 /* Launch plans and the autotuner                                            */
 /* ------------------------------------------------------------------------ */
 
-typedef enum { SINCOS_OP_PAIRS = 0, SINCOS_OP_BACKWARD = 1, SINCOS_OP_BATCHED = 2 } sincos_op;
+typedef enum {
+    SINCOS_OP_PAIRS = 0,
+    SINCOS_OP_BACKWARD = 1,
+    SINCOS_OP_BATCHED = 2,
+    SINCOS_OP_EXPI = 3
+} sincos_op;
 
 /* A launch configuration.
  * Register path (vec_bytes 16 or 32): threads per CTA, output vectors each
@@ -262,6 +267,10 @@ int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_d
                           int reduction, int coef, sincos_stream_t stream, sincos_plan *best);
 int sincos_autotune_backward(const float *gs, const float *gc, const float *s, const float *c,
                              float *gx, int64_t n, sincos_stream_t stream, sincos_plan *best);
+/* Same for sincos_expi on the caller's x and z (plans filed under
+ * SINCOS_OP_EXPI, dtype SINCOS_F32). */
+int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int coef,
+                         sincos_stream_t stream, sincos_plan *best);
 /* Same for the batched launch, timed on the caller's batch (outputs are
  * written); the plan is stored under (SINCOS_OP_BATCHED, out_dtype, bucket
  * of `count`), which is also the key batched calls look up. */

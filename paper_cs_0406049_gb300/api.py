@@ -18,7 +18,8 @@ _DTYPES = {torch.float32: _lib.F32, torch.bfloat16: _lib.BF16, torch.float16: _l
 _DTYPE_NAMES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
 _REDUCTIONS = {"plain": _lib.RED_PLAIN, "compensated": _lib.RED_COMPENSATED}
 _COEFS = {"normalized": _lib.COEF_NORMALIZED, "dagger": _lib.COEF_DAGGER}
-_OPS = {"pairs": _lib.OP_PAIRS, "backward": _lib.OP_BACKWARD, "batched": _lib.OP_BATCHED}
+_OPS = {"pairs": _lib.OP_PAIRS, "backward": _lib.OP_BACKWARD, "batched": _lib.OP_BATCHED,
+        "expi": _lib.OP_EXPI}
 
 
 def lib():
@@ -263,6 +264,18 @@ def sincos_autotune_pairs(x, s, c, reduction: str = "plain", coef: str = "normal
             _dev(x, "x", torch.float32), _dev(s, "s"), _dev(c, "c"), x.numel(),
             _DTYPES[s.dtype], _REDUCTIONS[reduction], _COEFS[coef], _stream(stream, x.device),
             ctypes.byref(p)), "sincos_autotune_pairs")
+    return p.as_dict()
+
+
+def sincos_autotune_expi(x, z, reduction: str = "plain", coef: str = "normalized",
+                         stream=None) -> dict:
+    p = _lib.sincos_plan()
+    zf = torch.view_as_real(z) if z.is_complex() else z
+    with torch.cuda.device(x.device):
+        check(lib().sincos_autotune_expi(_dev(x, "x", torch.float32), _dev(zf, "z"), x.numel(),
+                                         _REDUCTIONS[reduction], _COEFS[coef],
+                                         _stream(stream, x.device), ctypes.byref(p)),
+              "sincos_autotune_expi")
     return p.as_dict()
 
 

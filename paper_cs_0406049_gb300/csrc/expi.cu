@@ -5,8 +5,8 @@
 // per angle instead of two 4-byte ones, the same 12 bytes per angle.
 //
 // Register path: 4 angles per 16-byte load, 32 bytes of output per vector
-// (two 16-byte evict-first stores), the chunked grid-stride layout of
-// forward.cuh.  Bulk path: 8192-angle chunks through the two-stage TMA ring
+// (one 256-bit evict-first store when z allows, else two 16-byte stores), the
+// chunked grid-stride layout of forward.cuh.  Bulk path: 8192-angle chunks through the two-stage TMA ring
 // of bulk.cuh; each chunk's 64 KB of output leaves in one bulk store.
 #include "bulk.cuh"
 #include "core.cuh"
@@ -14,7 +14,10 @@
 
 namespace sincos_gb300 {
 
-template <int RED, int COEF>
+// Four angles to 32 bytes of (cos, sin) pairs: one 256-bit evict-first store
+// when z is 32-byte aligned (W = 32), so every 32-byte sector is written
+// whole by one instruction; two 16-byte stores otherwise (W = 16).
+template <int RED, int COEF, int W>
 __device__ __forceinline__ void expi_vec(const float *in, float *z)
 {
     float s0, s1, s2, s3, c0, c1, c2, c3;
@@ -22,12 +25,15 @@ __device__ __forceinline__ void expi_vec(const float *in, float *z)
     pair<RED, COEF>(in[1], s1, c1);
     pair<RED, COEF>(in[2], s2, c2);
     pair<RED, COEF>(in[3], s3, c3);
-    const uint32_t w0[4] = {__float_as_uint(c0), __float_as_uint(s0), __float_as_uint(c1),
-                            __float_as_uint(s1)};
-    const uint32_t w1[4] = {__float_as_uint(c2), __float_as_uint(s2), __float_as_uint(c3),
-                            __float_as_uint(s3)};
-    store_words<16>(z, w0);
-    store_words<16>(z + 4, w1);
+    const uint32_t w[8] = {__float_as_uint(c0), __float_as_uint(s0), __float_as_uint(c1),
+                           __float_as_uint(s1), __float_as_uint(c2), __float_as_uint(s2),
+                           __float_as_uint(c3), __float_as_uint(s3)};
+    if constexpr (W == 32) {
+        store_words<32>(z, w);
+    } else {
+        store_words<16>(z, w);
+        store_words<16>(z + 4, w + 4);
+    }
 }
 
 template <int RED, int COEF>
@@ -39,7 +45,7 @@ __device__ __forceinline__ void expi_elem(const float *x, float *z, int64_t i)
     z[2 * i + 1] = s;
 }
 
-template <int RED, int COEF, int UNROLL, int LD>
+template <int RED, int COEF, int UNROLL, int LD, int W>
 __global__ void k_expi(const float *x, float *z, int64_t n, int64_t head, int64_t nvec)
 {
     const float *xv = x + head;
@@ -53,13 +59,13 @@ __global__ void k_expi(const float *x, float *z, int64_t n, int64_t head, int64_
         for (int u = 0; u < UNROLL; ++u) ld16<LD>(in[u], xv + (v0 + (int64_t)u * blockDim.x) * 4);
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u)
-            expi_vec<RED, COEF>(in[u], zv + (v0 + (int64_t)u * blockDim.x) * 8);
+            expi_vec<RED, COEF, W>(in[u], zv + (v0 + (int64_t)u * blockDim.x) * 8);
     }
     if (blockIdx.x == (unsigned)(nfull % gridDim.x)) {
         for (int64_t v = nfull * chunk + threadIdx.x; v < nvec; v += blockDim.x) {
             float in[4];
             ld16<LD>(in, xv + v * 4);
-            expi_vec<RED, COEF>(in, zv + v * 8);
+            expi_vec<RED, COEF, W>(in, zv + v * 8);
         }
         for (int64_t i = threadIdx.x; i < head; i += blockDim.x) expi_elem<RED, COEF>(x, z, i);
         for (int64_t i = head + nvec * 4 + threadIdx.x; i < n; i += blockDim.x)
@@ -164,7 +170,7 @@ k_expi_bulk(const float *x, float *z, int64_t n, int64_t head, int64_t nchunks)
     for (int64_t v = blockIdx.x * (int64_t)NT + tid; v < nrest; v += (int64_t)gridDim.x * NT) {
         float in[4];
         ld16<LD_COHERENT>(in, xg + rest0 + v * 4);
-        expi_vec<RED, COEF>(in, zg + 2 * (rest0 + v * 4));
+        expi_vec<RED, COEF, 16>(in, zg + 2 * (rest0 + v * 4));
     }
     if (blockIdx.x == 0) {
         for (int64_t i = tid; i < head; i += NT) expi_elem<RED, COEF>(x, z, i);
@@ -174,23 +180,28 @@ k_expi_bulk(const float *x, float *z, int64_t n, int64_t head, int64_t nchunks)
 }
 
 // Where the vector grid starts: x + h and z + 2h both on a 128-byte line if
-// possible, else both 16-byte aligned; -1 if neither exists.
-static int expi_head(const float *x, const float *z)
+// possible, else x + h 16-byte and z + 2h 32-byte aligned (*w = 32), else both
+// 16-byte aligned (*w = 16); -1 if none exists.
+static int expi_head(const float *x, const float *z, int *w)
 {
     const uintptr_t ax = (uintptr_t)x, az = (uintptr_t)z;
+    *w = 32;
     if ((ax & 3u) || (az & 7u)) return -1;
     for (int h = 0; h < 32; ++h)
         if (((ax + 4u * h) & 127u) == 0 && ((az + 8u * h) & 127u) == 0) return h;
+    for (int h = 0; h < 8; ++h)
+        if (((ax + 4u * h) & 15u) == 0 && ((az + 8u * h) & 31u) == 0) return h;
+    *w = 16;
     for (int h = 0; h < 4; ++h)
         if (((ax + 4u * h) & 15u) == 0 && ((az + 8u * h) & 15u) == 0) return h;
     return -1;
 }
 
-template <int RED, int COEF, int UNROLL>
+template <int RED, int COEF, int UNROLL, int W>
 static int launch_expi_vec(const float *x, float *z, int64_t n, int64_t head,
                            const sincos_plan &plan, const DeviceInfo &dev, cudaStream_t st)
 {
-    const void *fn = (const void *)k_expi<RED, COEF, UNROLL, LD_NC>;
+    const void *fn = (const void *)k_expi<RED, COEF, UNROLL, LD_NC, W>;
     int per_sm = 0;
     const sincos_plan p = fit_plan(fn, plan, &per_sm);
     if (per_sm <= 0) return SINCOS_EUNSUPPORTED;
@@ -198,7 +209,7 @@ static int launch_expi_vec(const float *x, float *z, int64_t n, int64_t head,
     const int64_t chunks = nvec / ((int64_t)p.block * UNROLL);
     int64_t grid = (int64_t)per_sm * dev.sms;
     if (chunks < grid) grid = chunks > 0 ? chunks : 1;
-    k_expi<RED, COEF, UNROLL, LD_NC><<<(unsigned)grid, p.block, 0, st>>>(x, z, n, head, nvec);
+    k_expi<RED, COEF, UNROLL, LD_NC, W><<<(unsigned)grid, p.block, 0, st>>>(x, z, n, head, nvec);
     return check_launch("expi kernel launch");
 }
 
@@ -217,11 +228,24 @@ static int launch_expi_bulk(const float *x, float *z, int64_t n, int64_t head,
     return check_launch("expi bulk kernel launch");
 }
 
+template <int RED, int COEF, int W>
+static int launch_expi_w(const float *x, float *z, int64_t n, int64_t head,
+                         const sincos_plan &plan, const DeviceInfo &dev, cudaStream_t st)
+{
+    switch (plan.unroll) {
+    case 1:
+    case 2: return launch_expi_vec<RED, COEF, 2, W>(x, z, n, head, plan, dev, st);
+    case 4: return launch_expi_vec<RED, COEF, 4, W>(x, z, n, head, plan, dev, st);
+    default: return launch_expi_vec<RED, COEF, 8, W>(x, z, n, head, plan, dev, st);
+    }
+}
+
 template <int RED, int COEF>
 static int launch_expi_rc(const float *x, float *z, int64_t n, const sincos_plan &plan,
                           const DeviceInfo &dev, cudaStream_t st)
 {
-    const int h = expi_head(x, z);
+    int w = 16;
+    const int h = expi_head(x, z, &w);
     if (h < 0) {
         const void *fn = (const void *)k_expi_scalar<RED, COEF>;
         int per_sm = 0;
@@ -237,12 +261,22 @@ static int launch_expi_rc(const float *x, float *z, int64_t n, const sincos_plan
     if (plan_vec_bytes(plan) == 0 && n - head >= kBulkChunk)
         return plan.block == 256 ? launch_expi_bulk<RED, COEF, 256>(x, z, n, head, dev, st)
                                  : launch_expi_bulk<RED, COEF, 512>(x, z, n, head, dev, st);
-    switch (plan.unroll) {
-    case 1:
-    case 2: return launch_expi_vec<RED, COEF, 2>(x, z, n, head, plan, dev, st);
-    case 4: return launch_expi_vec<RED, COEF, 4>(x, z, n, head, plan, dev, st);
-    default: return launch_expi_vec<RED, COEF, 8>(x, z, n, head, plan, dev, st);
-    }
+    if (w == 32 && plan_vec_bytes(plan) != 16)
+        return launch_expi_w<RED, COEF, 32>(x, z, n, head, plan, dev, st);
+    return launch_expi_w<RED, COEF, 16>(x, z, n, head, plan, dev, st);
+}
+
+// Launch with an explicit plan (shared by the entry point and the autotuner).
+int launch_expi(const float *x, float *z, int64_t n, int red, int coef, const sincos_plan &plan,
+                const DeviceInfo &dev, cudaStream_t st)
+{
+    if (red == RED_PLAIN && coef == COEF_NORMALIZED)
+        return launch_expi_rc<RED_PLAIN, COEF_NORMALIZED>(x, z, n, plan, dev, st);
+    if (red == RED_COMPENSATED && coef == COEF_NORMALIZED)
+        return launch_expi_rc<RED_COMPENSATED, COEF_NORMALIZED>(x, z, n, plan, dev, st);
+    if (red == RED_PLAIN && coef == COEF_DAGGER)
+        return launch_expi_rc<RED_PLAIN, COEF_DAGGER>(x, z, n, plan, dev, st);
+    return launch_expi_rc<RED_COMPENSATED, COEF_DAGGER>(x, z, n, plan, dev, st);
 }
 
 unsigned take_timeouts_expi() { return take_bulk_wait_timeouts_here(); }
@@ -262,13 +296,6 @@ extern "C" int sincos_expi(const float *x, float *z, int64_t n, int reduction, i
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
-    const sincos_plan plan = plan_for(*dev, SINCOS_OP_PAIRS, SINCOS_F32, n);
-    cudaStream_t st = (cudaStream_t)stream;
-    if (reduction == RED_PLAIN && coef == COEF_NORMALIZED)
-        return launch_expi_rc<RED_PLAIN, COEF_NORMALIZED>(x, z, n, plan, *dev, st);
-    if (reduction == RED_COMPENSATED && coef == COEF_NORMALIZED)
-        return launch_expi_rc<RED_COMPENSATED, COEF_NORMALIZED>(x, z, n, plan, *dev, st);
-    if (reduction == RED_PLAIN && coef == COEF_DAGGER)
-        return launch_expi_rc<RED_PLAIN, COEF_DAGGER>(x, z, n, plan, *dev, st);
-    return launch_expi_rc<RED_COMPENSATED, COEF_DAGGER>(x, z, n, plan, *dev, st);
+    const sincos_plan plan = plan_for(*dev, SINCOS_OP_EXPI, SINCOS_F32, n);
+    return launch_expi(x, z, n, reduction, coef, plan, *dev, (cudaStream_t)stream);
 }

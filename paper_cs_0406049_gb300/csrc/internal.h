@@ -68,6 +68,8 @@ unsigned take_timeouts_expi();
 int launch_forward(const float *x, void *s, void *c, int64_t n, int dtype, int red, int coef,
                    bool in_place, const sincos_plan &plan, const DeviceInfo &dev,
                    cudaStream_t st);
+int launch_expi(const float *x, float *z, int64_t n, int red, int coef, const sincos_plan &plan,
+                const DeviceInfo &dev, cudaStream_t st);
 int launch_backward(const float *gs, const float *gc, const float *s, const float *c, float *gx,
                     int64_t n, bool in_place, const sincos_plan &plan, const DeviceInfo &dev,
                     cudaStream_t st);

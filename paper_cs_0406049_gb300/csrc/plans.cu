@@ -50,6 +50,7 @@ sincos_plan default_plan(int op, int dtype)
     // The binary32 single-array forward defaults to the bulk (TMA-staged)
     // path; 16-bit outputs run faster on the 32-byte register path.
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
+    if (op == SINCOS_OP_EXPI) return sincos_plan{512, 2, 1, 0};
     if (op == SINCOS_OP_BATCHED)
         return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
     return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
@@ -261,7 +262,7 @@ extern "C" {
 
 int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan)
 {
-    if (!plan || op < 0 || op > 2 || !valid_dtype(out_dtype) || n < 0) return SINCOS_EINVAL;
+    if (!plan || op < 0 || op > 3 || !valid_dtype(out_dtype) || n < 0) return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
@@ -271,7 +272,7 @@ int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan)
 
 int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan)
 {
-    if (!plan || op < 0 || op > 2 || !valid_dtype(out_dtype) || n < 0 || !plan_valid(*plan))
+    if (!plan || op < 0 || op > 3 || !valid_dtype(out_dtype) || n < 0 || !plan_valid(*plan))
         return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
@@ -299,6 +300,25 @@ int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_d
     return tune(*dev, SINCOS_OP_PAIRS, out_dtype, n, st,
                 [&](const sincos_plan &p) {
                     return launch_forward(x, s, c, n, out_dtype, reduction, coef, false, p, *dev, st);
+                },
+                best);
+}
+
+int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int coef,
+                         sincos_stream_t stream, sincos_plan *best)
+{
+    if (n <= 0 || !x || !z || !valid_reduction(reduction) || !valid_coef(coef))
+        return SINCOS_EINVAL;
+    const uintptr_t x0 = (uintptr_t)x, z0 = (uintptr_t)z;
+    if (x0 < z0 + 8u * (uint64_t)n && z0 < x0 + 4u * (uint64_t)n) return SINCOS_EOVERLAP;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    std::call_once(g_env_once, load_env_cache);
+    cudaStream_t st = (cudaStream_t)stream;
+    return tune(*dev, SINCOS_OP_EXPI, SINCOS_F32, n, st,
+                [&](const sincos_plan &p) {
+                    return launch_expi(x, z, n, reduction, coef, p, *dev, st);
                 },
                 best);
 }
