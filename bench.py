@@ -39,6 +39,12 @@ WORKLOAD = "bandwidth_2p28"
 WORKLOAD_DESC = ("2^28 float32 angles uniform in [-1000, 1000) (seed 1), float32 sin and cos "
                  "outputs (1 GiB in, 2 GiB out), plain reduction, normalized coefficients")
 BYTES_PER_PAIR = 12            # 4 B angle read + 4 B sine + 4 B cosine written
+# FP32 operations per Huygens term by its definition (an FMA, sqrt_rn and
+# rcp_rn count as one each): 3 differences, 3 for r^2, sqrt, reciprocal, k*r,
+# 26 for the pair with the compensated reduction, 4 for the complex product
+# and 2 accumulating FMAs.
+HUYGENS_OPS_PER_TERM = 41
+FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0      # only when the measured-peaks file is absent
 FWD_SOURCES = ["core.cuh", "bulk.cuh", "forward.cuh", "forward_f32.cu"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "ncu_forward_f32_bandwidth_2p28.md")
@@ -175,6 +181,14 @@ def measured_peak():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return HBM_FALLBACK_GBS, "fallback"
+
+
+def measured_sm_max_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 def kernel_source_sha() -> str:
@@ -361,6 +375,39 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
                                   "frac_of_peak": 12 * x.size / (ms * 1e-3) / 1e9 / peak,
                                   "plan": api.sincos_plan_get("expi", "f32", x.size)}
     del z, xt
+
+    # Huygens field sum (ALU-bound): 512 x 512 points, 4096 sources
+    w = workloads.diffraction()
+    P = tuple(torch.from_numpy(v).cuda() for v in w.p)
+    Q = tuple(torch.from_numpy(v).cuda() for v in w.q)
+    A = torch.from_numpy(w.a).cuda()
+    m, nsrc = w.p[0].size, w.q[0].size
+    u = torch.empty(m, dtype=torch.complex64, device="cuda")
+    if autotune:
+        api.sincos_autotune_huygens(P, Q, A, w.k, u)
+    sampler = ClockSampler(gpu_query_id(torch)) if dist.rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    t0 = time.time()
+    total, per, _ = time_loop(torch, lambda: api.sincos_huygens(P, Q, A, w.k, u),
+                              max(20, k // 4), 3, dist)
+    clocks = sampler.summary(t0, time.time()) if sampler else None
+    if sampler:
+        sampler.stop()
+    ms = statistics.mean(per)
+    terms = m * nsrc
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    max_mhz = measured_sm_max_mhz()
+    achieved = terms * HUYGENS_OPS_PER_TERM / (ms * 1e-3) / 1e12
+    peak_alu = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e12
+    out["diffraction_512x512_4096"] = {
+        "terms_per_s": terms / (ms * 1e-3), "ms": ms, "terms": terms,
+        "plan": api.sincos_plan_get("huygens", "f32", m),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu,
+                     "unit": "TFLOP32-ops/s", "frac": achieved / peak_alu,
+                     "peak_kind": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz} MHz",
+                     "ops_per_term": HUYGENS_OPS_PER_TERM},
+        "clocks": clocks}
+    del P, Q, A, u
 
     # backward: 2^26 angles U[-50, 50), gs, gc ~ N(0, 1): 20 B per element
     w = workloads.differentiation_inputs()

@@ -117,6 +117,35 @@ int sincos_expi(const float *x, float *z, int64_t n, int reduction, int coef,
                 sincos_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Fused consumer: Huygens-principle field sum                               */
+/* ------------------------------------------------------------------------ */
+
+/* The application the paper names (Sec. Conclusions: optical diffraction by
+ * Huygens' principle), with every phase factor made by the method in
+ * registers and never stored:
+ *   u_i = sum_{j<n} a_j exp(i k r_ij) / r_ij,  r_ij = |p_i - q_j|,
+ * in binary32 with this operation order per term:
+ *   d = p_i - q_j;  r = sqrt(fma(dz, dz, fma(dy, dy, dx*dx)));  w = 1/r;
+ *   (s, c) = the method's pair of k*r (normalized set, given reduction);
+ *   u_re = fma(w, fma(ar_j, c, -(ai_j*s)), u_re);
+ *   u_im = fma(w, fma(ar_j, s, ai_j*c), u_im);
+ * and the terms of each point summed in source order j = 0, 1, ... from 0,
+ * so the result is independent of the launch configuration.
+ *   px, py, pz  device, m floats each: observation points.
+ *   qx, qy, qz  device, n floats each: source points.
+ *   ar, ai      device, n floats each: complex source amplitudes.
+ *   k           wavenumber (2 pi / wavelength) in the coordinates' units.
+ *   reduction   SINCOS_RED_COMPENSATED recommended: phases k*r are large.
+ *   u           device, 2m floats, written as interleaved complex64; must not
+ *               overlap any input.
+ * A point that coincides with a source gives an infinite or NaN sum.
+ * n == 0 writes zeros.  Plan: SINCOS_OP_HUYGENS (SINCOS_F32). */
+int sincos_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                   const float *qx, const float *qy, const float *qz, const float *ar,
+                   const float *ai, int64_t n, float k, int reduction, float *u,
+                   sincos_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Backward                                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -230,7 +259,8 @@ typedef enum {
     SINCOS_OP_PAIRS = 0,
     SINCOS_OP_BACKWARD = 1,
     SINCOS_OP_BATCHED = 2,
-    SINCOS_OP_EXPI = 3
+    SINCOS_OP_EXPI = 3,
+    SINCOS_OP_HUYGENS = 4   /* plan: block = threads per CTA, unroll = points per thread */
 } sincos_op;
 
 /* A launch configuration.
@@ -271,6 +301,12 @@ int sincos_autotune_backward(const float *gs, const float *gc, const float *s, c
  * SINCOS_OP_EXPI, dtype SINCOS_F32). */
 int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int coef,
                          sincos_stream_t stream, sincos_plan *best);
+/* Same for sincos_huygens on the caller's buffers (plans filed under
+ * SINCOS_OP_HUYGENS, dtype SINCOS_F32, bucket of m). */
+int sincos_autotune_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                            const float *qx, const float *qy, const float *qz, const float *ar,
+                            const float *ai, int64_t n, float k, int reduction, float *u,
+                            sincos_stream_t stream, sincos_plan *best);
 /* Same for the batched launch, timed on the caller's batch (outputs are
  * written); the plan is stored under (SINCOS_OP_BATCHED, out_dtype, bucket
  * of `count`), which is also the key batched calls look up. */

@@ -91,6 +91,9 @@ class OracleLib:
         lib.oracle_sincos_f32_mt.restype = cint
         lib.oracle_round_16.argtypes = [f32p, u16p, i64, cint]
         lib.oracle_round_16.restype = None
+        lib.oracle_huygens.argtypes = [f32p, f32p, f32p, i64, f32p, f32p, f32p, f32p, f32p, i64,
+                                       ctypes.c_float, cint, f32p]
+        lib.oracle_huygens.restype = None
         self.path = path
         self._lib = lib
 
@@ -136,6 +139,22 @@ class OracleLib:
             _ptr(s, ctypes.c_float), _ptr(c, ctypes.c_float), _ptr(gx, ctypes.c_float), s.size)
         return gx
 
+    def huygens(self, p, q, a, k: float, reduction: str = "compensated") -> np.ndarray:
+        """Field sum at points p (3 x m) of sources q (3 x n) with complex
+        amplitudes a (n, complex): sum_j a_j exp(i k r_ij) / r_ij, every
+        phase factor from the method, summed in source order in binary32.
+        Returns complex64 (m,)."""
+        px, py, pz = (_f32(v) for v in p)
+        qx, qy, qz = (_f32(v) for v in q)
+        a = np.asarray(a, np.complex64).ravel()
+        ar, ai = _f32(a.real), _f32(a.imag)
+        m, n = px.size, qx.size
+        u = np.zeros(2 * m, np.float32)
+        f = lambda v: _ptr(v, ctypes.c_float)
+        self._lib.oracle_huygens(f(px), f(py), f(pz), m, f(qx), f(qy), f(qz), f(ar), f(ai), n,
+                                 float(np.float32(k)), REDUCTIONS[reduction], f(u))
+        return u.view(np.complex64)
+
     def round16(self, v, kind: str) -> np.ndarray:
         """Binary32 -> bf16 or fp16 bit patterns, round to nearest even."""
         v = _f32(v)
@@ -171,6 +190,24 @@ def to_bf16_bits(v) -> np.ndarray:
 
 def to_f16_bits(v) -> np.ndarray:
     return default().round16(v, "f16")
+
+
+def huygens(p, q, a, k: float, reduction: str = "compensated"):
+    return default().huygens(p, q, a, k, reduction)
+
+
+def huygens_fp64(p, q, a, k: float) -> np.ndarray:
+    """The same field sum in FP64 with libm sin/cos (error statement only)."""
+    P = np.stack([np.asarray(v, np.float32).astype(np.float64) for v in p], axis=1)
+    Q = np.stack([np.asarray(v, np.float32).astype(np.float64) for v in q], axis=1)
+    a = np.asarray(a, np.complex64).astype(np.complex128)
+    out = np.empty(P.shape[0], np.complex128)
+    kd = float(np.float32(k))
+    for i0 in range(0, P.shape[0], 256):
+        d = P[i0:i0 + 256, None, :] - Q[None, :, :]
+        r = np.sqrt((d * d).sum(axis=2))
+        out[i0:i0 + 256] = (a[None, :] * np.exp(1j * kd * r) / r).sum(axis=1)
+    return out
 
 
 def fp64_reference(x):

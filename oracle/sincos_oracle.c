@@ -259,6 +259,44 @@ void oracle_sincos_backward(const float *gs, const float *gc, const float *s,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Huygens-principle field sum (Sec. Conclusions: the method's application  */
+/* to optical diffraction), with the phase factor of every source-point     */
+/* pair produced by the method.  For observation point i and sources j:     */
+/*   dx = px_i - qx_j, dy, dz likewise                                       */
+/*   r  = sqrt(fma(dz, dz, fma(dy, dy, dx*dx)))      (correctly rounded)     */
+/*   w  = 1 / r                                      (correctly rounded)     */
+/*   (s, c) = the method's pair of theta = k * r     (given reduction)       */
+/*   pr = fma(ar_j, c, -(ai_j * s)),  pi = fma(ar_j, s, ai_j * c)            */
+/*   u_re = fma(w, pr, u_re),  u_im = fma(w, pi, u_im)                       */
+/* summed over j = 0, 1, ..., n-1 in that order from u = 0, in binary32.     */
+/* Result: u[2i] = u_re, u[2i+1] = u_im, i.e. sum_j a_j exp(i k r_ij) / r_ij.*/
+/* ------------------------------------------------------------------------ */
+
+void oracle_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                    const float *qx, const float *qy, const float *qz, const float *ar,
+                    const float *ai, int64_t n, float k, int reduction, float *u)
+{
+    for (int64_t i = 0; i < m; ++i) {
+        float ure = 0.0f, uim = 0.0f;
+        for (int64_t j = 0; j < n; ++j) {
+            float dx = px[i] - qx[j];
+            float dy = py[i] - qy[j];
+            float dz = pz[i] - qz[j];
+            float r = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            float w = 1.0f / r;
+            float s, c;
+            orc_pair(k * r, reduction, ORC_COEF_NORMALIZED, &s, &c);
+            float pr = fmaf(ar[j], c, -(ai[j] * s));
+            float pi = fmaf(ar[j], s, ai[j] * c);
+            ure = fmaf(w, pr, ure);
+            uim = fmaf(w, pi, uim);
+        }
+        u[2 * i] = ure;
+        u[2 * i + 1] = uim;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Threaded driver, used only to time the oracle as a CPU baseline: a static */
 /* contiguous split of [0, n) over nthreads POSIX threads.                   */
 /* ------------------------------------------------------------------------ */

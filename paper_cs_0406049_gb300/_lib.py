@@ -17,7 +17,7 @@ OK, EINVAL, EOVERLAP, ECUDA, EUNSUPPORTED, ECAPTURE = 0, -1, -2, -3, -4, -5
 F32, BF16, F16 = 0, 1, 2
 RED_PLAIN, RED_COMPENSATED = 0, 1
 COEF_NORMALIZED, COEF_DAGGER = 0, 1
-OP_PAIRS, OP_BACKWARD, OP_BATCHED, OP_EXPI = 0, 1, 2, 3
+OP_PAIRS, OP_BACKWARD, OP_BATCHED, OP_EXPI, OP_HUYGENS = 0, 1, 2, 3, 4
 NOALLOC_MAX_SEGMENTS = 65536
 
 
@@ -42,6 +42,8 @@ SIGNATURES = {
     "sincos_pairs_ex": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP]),
     "sincos_expi": (_INT, [_VP, _VP, _I64, _INT, _INT, _VP]),
     "sincos_backward": (_INT, [_VP, _VP, _VP, _VP, _VP, _I64, _VP]),
+    "sincos_huygens": (_INT, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, ctypes.c_float,
+                              _INT, _VP, _VP]),
     "sincos_batched": (_INT, [_VP, _VP, _INT, _VP]),
     "sincos_batched_ex": (_INT, [_VP, _VP, _INT, _INT, _INT, _INT, _VP]),
     "sincos_batched_release": (_INT, []),
@@ -57,6 +59,8 @@ SIGNATURES = {
     "sincos_autotune_pairs": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _PLANP]),
     "sincos_autotune_backward": (_INT, [_VP, _VP, _VP, _VP, _VP, _I64, _VP, _PLANP]),
     "sincos_autotune_expi": (_INT, [_VP, _VP, _I64, _INT, _INT, _VP, _PLANP]),
+    "sincos_autotune_huygens": (_INT, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64,
+                                       ctypes.c_float, _INT, _VP, _VP, _PLANP]),
     "sincos_autotune_batched": (_INT, [_VP, _VP, _INT, _INT, _INT, _INT, _VP, _PLANP]),
     "sincos_plan_cache_save": (_INT, [ctypes.c_char_p]),
     "sincos_plan_cache_load": (_INT, [ctypes.c_char_p]),

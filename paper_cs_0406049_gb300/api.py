@@ -19,7 +19,7 @@ _DTYPE_NAMES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float
 _REDUCTIONS = {"plain": _lib.RED_PLAIN, "compensated": _lib.RED_COMPENSATED}
 _COEFS = {"normalized": _lib.COEF_NORMALIZED, "dagger": _lib.COEF_DAGGER}
 _OPS = {"pairs": _lib.OP_PAIRS, "backward": _lib.OP_BACKWARD, "batched": _lib.OP_BATCHED,
-        "expi": _lib.OP_EXPI}
+        "expi": _lib.OP_EXPI, "huygens": _lib.OP_HUYGENS}
 
 
 def lib():
@@ -105,6 +105,55 @@ def expi(x: torch.Tensor, reduction: str = "plain", coef: str = "normalized") ->
     z = torch.empty(x.shape, dtype=torch.complex64, device=x.device)
     sincos_expi(x.contiguous(), z, reduction, coef)
     return z
+
+
+def _huygens_args(p, q, a, u):
+    px, py, pz = p
+    qx, qy, qz = q
+    a = a if a.is_complex() else torch.complex(a, torch.zeros_like(a))
+    af = torch.view_as_real(a.contiguous())
+    ar, ai = af[:, 0].contiguous(), af[:, 1].contiguous()
+    uf = torch.view_as_real(u) if u.is_complex() else u
+    m, n = px.numel(), qx.numel()
+    if uf.numel() != 2 * m:
+        raise ValueError("u must be complex64 with m elements or float32 with 2m")
+    ptrs = [_dev(t, name, torch.float32) for t, name in
+            ((px, "px"), (py, "py"), (pz, "pz"), (qx, "qx"), (qy, "qy"), (qz, "qz"),
+             (ar, "ar"), (ai, "ai"))]
+    return ptrs, m, n, _dev(uf, "u", torch.float32), (ar, ai)
+
+
+def sincos_huygens(p, q, a: torch.Tensor, k: float, u: torch.Tensor,
+                   reduction: str = "compensated", stream=None) -> None:
+    """u_i = sum_j a_j exp(i k |p_i - q_j|) / |p_i - q_j|; p and q are (x, y, z)
+    triples of float32 CUDA tensors, a complex (or real) amplitudes."""
+    ptrs, m, n, up, keep = _huygens_args(p, q, a, u)
+    with torch.cuda.device(u.device):
+        check(lib().sincos_huygens(ptrs[0], ptrs[1], ptrs[2], m, ptrs[3], ptrs[4], ptrs[5],
+                                   ptrs[6], ptrs[7], n, float(k), _REDUCTIONS[reduction], up,
+                                   _stream(stream, u.device)), "sincos_huygens")
+        del keep
+
+
+def huygens(p, q, a: torch.Tensor, k: float, reduction: str = "compensated") -> torch.Tensor:
+    """The Huygens field sum as a new complex64 tensor of the points' size."""
+    u = torch.empty(p[0].numel(), dtype=torch.complex64, device=p[0].device)
+    sincos_huygens(p, q, a, k, u, reduction)
+    return u
+
+
+def sincos_autotune_huygens(p, q, a, k: float, u, reduction: str = "compensated",
+                            stream=None) -> dict:
+    ptrs, m, n, up, keep = _huygens_args(p, q, a, u)
+    plan = _lib.sincos_plan()
+    with torch.cuda.device(u.device):
+        check(lib().sincos_autotune_huygens(ptrs[0], ptrs[1], ptrs[2], m, ptrs[3], ptrs[4],
+                                            ptrs[5], ptrs[6], ptrs[7], n, float(k),
+                                            _REDUCTIONS[reduction], up,
+                                            _stream(stream, u.device), ctypes.byref(plan)),
+              "sincos_autotune_huygens")
+        del keep
+    return plan.as_dict()
 
 
 def sincos_backward(gs, gc, s: torch.Tensor, c: torch.Tensor, gx: torch.Tensor,

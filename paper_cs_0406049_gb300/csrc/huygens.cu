@@ -1,0 +1,168 @@
+// huygens.cu -- Huygens-principle field sum with the method's phase factors
+// generated in registers (the application the paper names in its
+// conclusions: optical diffraction patterns by Huygens' principle).
+//
+//   u_i = sum_j a_j exp(i k r_ij) / r_ij,   r_ij = |p_i - q_j|
+//
+// Each term, in binary32 with explicit roundings:
+//   d = p_i - q_j;  r = sqrt_rn(fma(dz, dz, fma(dy, dy, dx*dx)));  w = rcp_rn(r)
+//   (s, c) = pair(k*r)                       (core.cuh, normalized set)
+//   u_re = fma(w, fma(ar, c, -(ai*s)), u_re);  u_im = fma(w, fma(ar, s, ai*c), u_im)
+// summed over j in source order from 0, so the result does not depend on the
+// launch configuration.
+//
+// Schedule.  A thread owns P consecutive observation points and keeps their
+// coordinates and sums in registers.  Sources stream through shared memory
+// in tiles of kHuyTile; inside a tile every thread reads the same source at
+// the same time (a broadcast), so each source costs two shared loads per P
+// terms of about 40 FP32 operations each.  The kernel is FP32-pipe bound.
+#include "core.cuh"
+#include "internal.h"
+
+namespace sincos_gb300 {
+
+constexpr int kHuyTile = 2048;
+
+template <int RED, int P>
+__global__ void k_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                          const float *qx, const float *qy, const float *qz, const float *ar,
+                          const float *ai, int64_t n, float k, float *u)
+{
+    __shared__ float4 sq[kHuyTile];        // qx, qy, qz, ar
+    __shared__ float sai[kHuyTile];        // ai
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * P;
+    float x[P], y[P], z[P], ure[P], uim[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int64_t i = i0 + p < m ? i0 + p : m - 1;     // tail threads repeat the last point
+        x[p] = px[i];
+        y[p] = py[i];
+        z[p] = pz[i];
+        ure[p] = 0.0f;
+        uim[p] = 0.0f;
+    }
+    for (int64_t j0 = 0; j0 < n; j0 += kHuyTile) {
+        const int cnt = (int)(n - j0 < kHuyTile ? n - j0 : kHuyTile);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            sq[t] = make_float4(qx[j0 + t], qy[j0 + t], qz[j0 + t], ar[j0 + t]);
+            sai[t] = ai[j0 + t];
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int t = 0; t < cnt; ++t) {
+            const float4 q = sq[t];
+            const float aim = sai[t];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float dx = __fsub_rn(x[p], q.x);
+                const float dy = __fsub_rn(y[p], q.y);
+                const float dz = __fsub_rn(z[p], q.z);
+                const float r =
+                    __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+                const float w = __frcp_rn(r);
+                float s, c;
+                pair<RED, COEF_NORMALIZED>(__fmul_rn(k, r), s, c);
+                const float pr = __fmaf_rn(q.w, c, -__fmul_rn(aim, s));
+                const float pi = __fmaf_rn(q.w, s, __fmul_rn(aim, c));
+                ure[p] = __fmaf_rn(w, pr, ure[p]);
+                uim[p] = __fmaf_rn(w, pi, uim[p]);
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        if (i0 + p < m) {
+            u[2 * (i0 + p)] = ure[p];
+            u[2 * (i0 + p) + 1] = uim[p];
+        }
+    }
+}
+
+template <int RED, int P>
+static int launch_huygens_p(const float *px, const float *py, const float *pz, int64_t m,
+                            const float *qx, const float *qy, const float *qz, const float *ar,
+                            const float *ai, int64_t n, float k, float *u,
+                            const sincos_plan &plan, cudaStream_t st)
+{
+    const void *fn = (const void *)k_huygens<RED, P>;
+    int per_sm = 0;
+    const sincos_plan p = fit_plan(fn, plan, &per_sm);
+    if (per_sm <= 0) return SINCOS_EUNSUPPORTED;
+    const int64_t per_cta = (int64_t)p.block * P;
+    const int64_t grid = (m + per_cta - 1) / per_cta;
+    if (grid > 0x7fffffff) return SINCOS_EUNSUPPORTED;
+    k_huygens<RED, P><<<(unsigned)grid, p.block, 0, st>>>(px, py, pz, m, qx, qy, qz, ar, ai, n,
+                                                           k, u);
+    return check_launch("huygens kernel launch");
+}
+
+template <int RED>
+static int launch_huygens_r(const float *px, const float *py, const float *pz, int64_t m,
+                            const float *qx, const float *qy, const float *qz, const float *ar,
+                            const float *ai, int64_t n, float k, float *u,
+                            const sincos_plan &plan, cudaStream_t st)
+{
+    switch (plan.unroll) {
+    case 1: return launch_huygens_p<RED, 1>(px, py, pz, m, qx, qy, qz, ar, ai, n, k, u, plan, st);
+    case 2: return launch_huygens_p<RED, 2>(px, py, pz, m, qx, qy, qz, ar, ai, n, k, u, plan, st);
+    default: return launch_huygens_p<RED, 4>(px, py, pz, m, qx, qy, qz, ar, ai, n, k, u, plan, st);
+    }
+}
+
+int launch_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                   const float *qx, const float *qy, const float *qz, const float *ar,
+                   const float *ai, int64_t n, float k, int red, float *u,
+                   const sincos_plan &plan, cudaStream_t st)
+{
+    if (red == RED_COMPENSATED)
+        return launch_huygens_r<RED_COMPENSATED>(px, py, pz, m, qx, qy, qz, ar, ai, n, k, u, plan,
+                                                 st);
+    return launch_huygens_r<RED_PLAIN>(px, py, pz, m, qx, qy, qz, ar, ai, n, k, u, plan, st);
+}
+
+}  // namespace sincos_gb300
+
+using namespace sincos_gb300;
+
+namespace {
+
+bool overlaps_output(const float *in, int64_t cnt, const float *u, int64_t m)
+{
+    const uintptr_t a0 = (uintptr_t)in, a1 = a0 + 4u * (uint64_t)cnt;
+    const uintptr_t b0 = (uintptr_t)u, b1 = b0 + 8u * (uint64_t)m;
+    return a0 < b1 && b0 < a1;
+}
+
+int huygens_check(const float *px, const float *py, const float *pz, int64_t m,
+                  const float *qx, const float *qy, const float *qz, const float *ar,
+                  const float *ai, int64_t n, int reduction, float *u)
+{
+    if (m < 0 || n < 0 || !valid_reduction(reduction)) return SINCOS_EINVAL;
+    if (m == 0) return SINCOS_OK;
+    if (!px || !py || !pz || !u) return SINCOS_EINVAL;
+    if (n > 0 && (!qx || !qy || !qz || !ar || !ai)) return SINCOS_EINVAL;
+    for (const float *p : {px, py, pz})
+        if (overlaps_output(p, m, u, m)) return SINCOS_EOVERLAP;
+    if (n > 0)
+        for (const float *q : {qx, qy, qz, ar, ai})
+            if (overlaps_output(q, n, u, m)) return SINCOS_EOVERLAP;
+    return 1;   // valid, work to do
+}
+
+}  // namespace
+
+extern "C" int sincos_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                              const float *qx, const float *qy, const float *qz,
+                              const float *ar, const float *ai, int64_t n, float k,
+                              int reduction, float *u, sincos_stream_t stream)
+{
+    int rc = huygens_check(px, py, pz, m, qx, qy, qz, ar, ai, n, reduction, u);
+    if (rc != 1) return rc;
+    const DeviceInfo *dev = nullptr;
+    rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    const sincos_plan plan = plan_for(*dev, SINCOS_OP_HUYGENS, SINCOS_F32, m);
+    return launch_huygens(px, py, pz, m, qx, qy, qz, ar, ai, n, k, reduction, u, plan,
+                          (cudaStream_t)stream);
+}

@@ -70,6 +70,10 @@ int launch_forward(const float *x, void *s, void *c, int64_t n, int dtype, int r
                    cudaStream_t st);
 int launch_expi(const float *x, float *z, int64_t n, int red, int coef, const sincos_plan &plan,
                 const DeviceInfo &dev, cudaStream_t st);
+int launch_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                   const float *qx, const float *qy, const float *qz, const float *ar,
+                   const float *ai, int64_t n, float k, int red, float *u,
+                   const sincos_plan &plan, cudaStream_t st);
 int launch_backward(const float *gs, const float *gc, const float *s, const float *c, float *gx,
                     int64_t n, bool in_place, const sincos_plan &plan, const DeviceInfo &dev,
                     cudaStream_t st);

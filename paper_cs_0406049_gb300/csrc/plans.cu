@@ -51,6 +51,7 @@ sincos_plan default_plan(int op, int dtype)
     // path; 16-bit outputs run faster on the 32-byte register path.
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
     if (op == SINCOS_OP_EXPI) return sincos_plan{512, 2, 1, 0};
+    if (op == SINCOS_OP_HUYGENS) return sincos_plan{256, 2, 8, 16};
     if (op == SINCOS_OP_BATCHED)
         return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
     return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
@@ -155,6 +156,11 @@ void store_plan(const DeviceInfo &dev, int op, int dtype, int64_t n, const sinco
 std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
 {
     std::vector<sincos_plan> out;
+    if (op == SINCOS_OP_HUYGENS) {  // CTA size and points per thread only
+        for (int block : {128, 256, 512})
+            for (int pts : {1, 2, 4}) out.push_back(sincos_plan{block, pts, 8, 16});
+        return out;
+    }
     if (op != SINCOS_OP_BACKWARD)   // bulk path: one CTA per SM, CTA size only
         for (int block : {128, 256, 512, 1024}) out.push_back(sincos_plan{block, 2, 1, 0});
     const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
@@ -262,7 +268,7 @@ extern "C" {
 
 int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan)
 {
-    if (!plan || op < 0 || op > 3 || !valid_dtype(out_dtype) || n < 0) return SINCOS_EINVAL;
+    if (!plan || op < 0 || op > 4 || !valid_dtype(out_dtype) || n < 0) return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
@@ -272,7 +278,7 @@ int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan)
 
 int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan)
 {
-    if (!plan || op < 0 || op > 3 || !valid_dtype(out_dtype) || n < 0 || !plan_valid(*plan))
+    if (!plan || op < 0 || op > 4 || !valid_dtype(out_dtype) || n < 0 || !plan_valid(*plan))
         return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
@@ -319,6 +325,27 @@ int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int
     return tune(*dev, SINCOS_OP_EXPI, SINCOS_F32, n, st,
                 [&](const sincos_plan &p) {
                     return launch_expi(x, z, n, reduction, coef, p, *dev, st);
+                },
+                best);
+}
+
+int sincos_autotune_huygens(const float *px, const float *py, const float *pz, int64_t m,
+                            const float *qx, const float *qy, const float *qz, const float *ar,
+                            const float *ai, int64_t n, float k, int reduction, float *u,
+                            sincos_stream_t stream, sincos_plan *best)
+{
+    if (m <= 0 || n < 0 || !px || !py || !pz || !u || !valid_reduction(reduction))
+        return SINCOS_EINVAL;
+    if (n > 0 && (!qx || !qy || !qz || !ar || !ai)) return SINCOS_EINVAL;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    std::call_once(g_env_once, load_env_cache);
+    cudaStream_t st = (cudaStream_t)stream;
+    return tune(*dev, SINCOS_OP_HUYGENS, SINCOS_F32, m, st,
+                [&](const sincos_plan &p) {
+                    return launch_huygens(px, py, pz, m, qx, qy, qz, ar, ai, n, k, reduction, u,
+                                          p, st);
                 },
                 best);
 }

@@ -21,7 +21,7 @@ from . import api, build
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--op", choices=["forward", "forward_bf16", "forward_compensated",
-                                    "backward", "batched"], default="forward")
+                                    "backward", "batched", "expi", "huygens"], default="forward")
     p.add_argument("--log2n", type=int, default=26)
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--plan", default="",
@@ -44,6 +44,19 @@ def main(argv=None):
         c = torch.empty_like(s)
         use_plan("pairs", dt, n)
         run = lambda: api.sincos_pairs_ex(x, s, c, red)
+    elif a.op == "expi":
+        z = torch.empty(n, dtype=torch.complex64, device="cuda")
+        use_plan("expi", "f32", n)
+        run = lambda: api.sincos_expi(x, z)
+    elif a.op == "huygens":
+        # n observation points on a plane at z = 400, 4096 sources in a disc
+        pts = (x[:n] * 0.06, torch.flip(x[:n], [0]) * 0.06, torch.full((n,), 400.0, device="cuda"))
+        src = (x[:4096] * 0.014, x[4096:8192] * 0.014, torch.zeros(4096, device="cuda"))
+        amp = torch.complex(torch.randn(4096, device="cuda", generator=g),
+                            torch.randn(4096, device="cuda", generator=g))
+        u = torch.empty(n, dtype=torch.complex64, device="cuda")
+        use_plan("huygens", "f32", n)
+        run = lambda: api.sincos_huygens(pts, src, amp, 6.2831855, u)
     elif a.op == "backward":
         gs = torch.randn(n, device="cuda", generator=g)
         gc = torch.randn(n, device="cuda", generator=g)

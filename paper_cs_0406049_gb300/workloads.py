@@ -94,6 +94,42 @@ def differentiation(n: int, lo: float, hi: float, seed: int) -> Differentiation:
     return Differentiation(x, gs, gc)
 
 
+@dataclass
+class Diffraction:
+    """Observation points p (3 arrays of m), sources q (3 arrays of n), complex
+    amplitudes a (n,) and the wavenumber k, in units of the wavelength."""
+    p: tuple
+    q: tuple
+    a: np.ndarray
+    k: float
+
+
+def diffraction(grid: int = 512, half_width: float = 60.0, distance: float = 400.0,
+                sources: int = 4096, radius: float = 20.0, seed: int = 5) -> Diffraction:
+    """A grid x grid observation plane at z = distance spanning
+    [-half_width, half_width]^2; `sources` points uniform in a disc of the
+    given radius at z = 0 (pairs drawn uniform in the enclosing square, in
+    batches, keeping those inside the disc in draw order); then complex
+    Gaussian amplitudes.  Lengths in wavelengths, so k = 2 pi."""
+    rng = np.random.default_rng(seed)
+    g = np.linspace(-half_width, half_width, grid)
+    gx, gy = np.meshgrid(g, g, indexing="xy")
+    p = (gx.ravel().astype(np.float32), gy.ravel().astype(np.float32),
+         np.full(grid * grid, distance, np.float32))
+    xs, ys = [], []
+    kept = 0
+    while kept < sources:
+        cand = rng.uniform(-radius, radius, (2 * sources, 2))
+        inside = cand[(cand * cand).sum(axis=1) <= radius * radius]
+        xs.append(inside[:, 0])
+        ys.append(inside[:, 1])
+        kept += inside.shape[0]
+    q = (np.concatenate(xs)[:sources].astype(np.float32),
+         np.concatenate(ys)[:sources].astype(np.float32), np.zeros(sources, np.float32))
+    a = (rng.standard_normal(sources) + 1j * rng.standard_normal(sources)).astype(np.complex64)
+    return Diffraction(p, q, a, float(np.float32(2.0 * np.pi)))
+
+
 # -- the five workloads the path is measured and checked on --------------------
 
 PLAIN_N = 1 << 20            # uniform in [-pi, pi), seed 0
@@ -109,6 +145,9 @@ WORKLOADS = {
                       "bf16/f16",
     "batching_4096": "4096 arrays, len=clamp(round(2^(20U)),1,2^20), U[-100,100), seed 3",
     "differentiation_2p26": "2^26 angles U[-50, 50), seed 4; gs, gc ~ N(0,1) f32",
+    "diffraction_512x512_4096": "512x512 observation grid at z=400 over [-60,60]^2, 4096 "
+                                "sources uniform in a radius-20 disc, Gaussian amplitudes, "
+                                "k=2pi, seed 5",
 }
 
 

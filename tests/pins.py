@@ -384,9 +384,82 @@ def pin_backward(lib, n: int = 4096):
     assert np.all(lib.backward(None, None, s, c) == 0.0)
 
 
+# ----------------------------------------------------------------------------
+# Huygens field sum.
+# ----------------------------------------------------------------------------
+
+def huygens_case(m=48, n=300, seed=21, distance=400.0):
+    rng = np.random.default_rng(seed)
+    p = (rng.uniform(-60, 60, m).astype(np.float32), rng.uniform(-60, 60, m).astype(np.float32),
+         np.full(m, distance, np.float32))
+    q = (rng.uniform(-14, 14, n).astype(np.float32), rng.uniform(-14, 14, n).astype(np.float32),
+         rng.uniform(-1, 1, n).astype(np.float32))
+    a = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    return p, q, a, float(np.float32(2 * np.pi))
+
+
+def pin_huygens_fp64(lib):
+    """Against the FP64 sum of a_j exp(i k r)/r with libm: every point within
+    the per-term bound sum_j |a_j|/r_ij (k r_ij 2^-22 + 1.5e-6) (binary32
+    rounding of r and of k r, plus the method's error) plus the sequential
+    binary32 summation bound n 2^-24 sum_j |a_j|/r_ij."""
+    import oracle
+    for red in ("compensated", "plain"):
+        p, q, a, k = huygens_case()
+        u = lib.huygens(p, q, a, k, red).astype(np.complex128)
+        ref = oracle.huygens_fp64(p, q, a, k)
+        P = np.stack([v.astype(np.float64) for v in p], 1)
+        Q = np.stack([v.astype(np.float64) for v in q], 1)
+        r = np.sqrt(((P[:, None, :] - Q[None, :, :]) ** 2).sum(2))
+        t = np.abs(a.astype(np.complex128))[None, :] / r
+        method = 1.5e-6 if red == "compensated" else 1.5e-6 + 2 * np.pi * (k * r / (2 * np.pi)) * 2.0 ** -23
+        bound = (t * (k * r * 2.0 ** -22 + method)).sum(1) + q[0].size * 2.0 ** -24 * t.sum(1)
+        assert np.all(np.abs(u - ref) <= bound), (red, np.max(np.abs(u - ref) / bound))
+
+
+def pin_huygens_airy(lib):
+    """Far field of a uniformly lit circular aperture (Fraunhofer, Fresnel
+    number 0.01): |u|^2 / |u(0)|^2 follows (2 J1(v)/v)^2 with v = k a sin(t),
+    the Airy pattern, to within 0.01 over the first three lobes."""
+    from scipy.special import j1
+    radius, spacing, z = 10.0, 0.25, 1.0e4
+    g = np.arange(-radius, radius + spacing / 2, spacing)
+    gx, gy = np.meshgrid(g, g)
+    keep = gx * gx + gy * gy <= radius * radius
+    q = (gx[keep].astype(np.float32), gy[keep].astype(np.float32),
+         np.zeros(int(keep.sum()), np.float32))
+    a = np.ones(q[0].size, np.complex64)
+    ang = np.linspace(0.0, 0.15, 61)
+    p = ((z * np.tan(ang)).astype(np.float32), np.zeros(ang.size, np.float32),
+         np.full(ang.size, z, np.float32))
+    k = float(np.float32(2 * np.pi))
+    u = lib.huygens(p, q, a, k, "compensated").astype(np.complex128)
+    inten = np.abs(u) ** 2 / np.abs(u[0]) ** 2
+    v = k * radius * np.sin(ang)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        airy = np.where(v == 0, 1.0, (2 * j1(v) / v) ** 2)
+    assert np.max(np.abs(inten - airy)) < 0.01, np.max(np.abs(inten - airy))
+
+
+def pin_huygens_edges(lib):
+    """No sources: a zero field.  One source: a single term, a exp(i k r)/r,
+    within the per-term bound of pin_huygens_fp64 (no summation error)."""
+    p, q, a, k = huygens_case(m=7, n=1)
+    z = lib.huygens(p, (q[0][:0], q[1][:0], q[2][:0]), a[:0], k)
+    assert np.all(z == 0)
+    u = lib.huygens(p, q, a, k, "compensated").astype(np.complex128)
+    P = np.stack([v.astype(np.float64) for v in p], 1)
+    Q = np.array([q[0][0], q[1][0], q[2][0]], np.float64)
+    r = np.sqrt(((P - Q) ** 2).sum(1))
+    ref = complex(a[0]) * np.exp(1j * float(k) * r) / r
+    bound = abs(complex(a[0])) / r * (k * r * 2.0 ** -22 + 1.5e-6)
+    assert np.all(np.abs(u - ref) <= bound)
+
+
 ALL_PINS = [
     pin_e1_normalized, pin_e2_dagger, pin_drift_correction, pin_bruteforce, pin_symmetry,
     pin_periodicity, pin_exact_at_whole_turns, pin_quarter_turns, pin_ties_to_even,
     pin_special_values, pin_plain_reduction_bound, pin_compensated, pin_bf16_rounding,
-    pin_f16_rounding, pin_16bit_outputs, pin_backward,
+    pin_f16_rounding, pin_16bit_outputs, pin_backward, pin_huygens_fp64, pin_huygens_airy,
+    pin_huygens_edges,
 ]

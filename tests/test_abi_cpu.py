@@ -130,3 +130,17 @@ def test_plan_validation(lib):
     assert lib.sincos_plan_set(9, 0, 1 << 20, ctypes.byref(good)) == _lib.EINVAL
     assert lib.sincos_plan_get(0, 0, 1 << 20, None) == _lib.EINVAL
     assert lib.sincos_plan_cache_load(b"/nonexistent/path.json") == _lib.EINVAL
+
+
+def test_huygens_validation(lib):
+    f = lambda *a: lib.sincos_huygens(*a)
+    P = (A, A + 4096, A + 8192)
+    Q = (A + 12288, A + 16384, A + 20480, A + 24576, A + 28672)
+    U = A + 65536
+    assert f(*P, -1, *Q, 8, 6.28, 1, U, None) == _lib.EINVAL
+    assert f(*P, 8, *Q, -1, 6.28, 1, U, None) == _lib.EINVAL
+    assert f(*P, 8, *Q, 8, 6.28, 7, U, None) == _lib.EINVAL
+    assert f(None, A + 4096, A + 8192, 8, *Q, 8, 6.28, 1, U, None) == _lib.EINVAL
+    assert f(*P, 8, None, *Q[1:], 8, 6.28, 1, U, None) == _lib.EINVAL
+    assert f(*P, 8, *Q, 8, 6.28, 1, A + 4, None) == _lib.EOVERLAP      # u over px
+    assert f(*P, 0, *Q, 8, 6.28, 1, U, None) == _lib.OK

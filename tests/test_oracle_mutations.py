@@ -52,6 +52,13 @@ MUTATIONS = {
     "backward_swapped_operands": [("gx[i] = fmaf(gs[i], c[i], -(gc[i] * s[i]));",
                                    "gx[i] = fmaf(gs[i], s[i], -(gc[i] * c[i]));")],
     "backward_null_gc_sign": [("gx[i] = gs[i] * c[i];", "gx[i] = -(gs[i] * c[i]);")],
+    # Huygens sum
+    "huygens_conjugate": [("float pi = fmaf(ar[j], s, ai[j] * c);",
+                           "float pi = fmaf(ar[j], -s, ai[j] * c);")],
+    "huygens_no_falloff": [("ure = fmaf(w, pr, ure);\n            uim = fmaf(w, pi, uim);",
+                            "ure = pr + ure;\n            uim = pi + uim;")],
+    "huygens_dropped_dz": [("float r = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));",
+                            "float r = sqrtf(fmaf(dy, dy, dx * dx));")],
 }
 
 # cheapest first; the expensive statistics run only if nothing cheaper fails
@@ -63,6 +70,7 @@ PIN_ORDER = [
     pins.pin_drift_correction,
     functools.partial(pins.pin_e1_normalized, n=1 << 22),
     functools.partial(pins.pin_e2_dagger, n=1 << 22),
+    pins.pin_huygens_fp64, pins.pin_huygens_edges,
     pins.pin_bruteforce,
 ]
 
