@@ -334,6 +334,31 @@ def cpu_baseline(x: np.ndarray) -> dict:
                       f"{dt:.1f} s wall on {used} threads"}
 
 
+def cuda_libm_context(torch, x_np, x, s, c, dist, steps: int) -> dict:
+    """CUDA's sincosf and __sincosf on the same 2^28 angles and buffers, for
+    context: GB/s and FP64 errors on a sample."""
+    import ctypes
+    from paper_cs_0406049_gb300 import build as libbuild
+    lib = ctypes.CDLL(libbuild.build_context())
+    lib.context_libm_sincos.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    out = {}
+    n = x.numel()
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, n, 1 << 20)
+    it = torch.from_numpy(idx).cuda()
+    for name, fast in (("sincosf", 0), ("__sincosf", 1)):
+        st = torch.cuda.current_stream().cuda_stream
+        run = lambda: lib.context_libm_sincos(x.data_ptr(), s.data_ptr(), c.data_ptr(), n, fast, st)
+        total, per, _ = time_loop(torch, run, steps, 3, dist)
+        ms = statistics.mean(per)
+        err = fp64_errors(x_np[idx], s[it].cpu().numpy().astype(np.float64),
+                          c[it].cpu().numpy().astype(np.float64))
+        out[name] = {"pairs_per_s": n / (ms * 1e-3), "gbs": 12 * n / (ms * 1e-3) / 1e9,
+                     "errors": err}
+    return out
+
+
 def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict:
     """Secondary workloads, each with its own GB/s and errors (not the headline)."""
     out = {}
@@ -553,8 +578,10 @@ def run_ours(args, dist: Dist):
 
     ext = None
     if not args.no_extras:
+        libm = cuda_libm_context(torch, x_np, x, s, c, dist, max(20, min(args.steps, 100)))
         del s, c
         ext = extras(torch, api, workloads, dist, args.steps, not args.no_autotune)
+        ext["context_cuda_libm_2p28"] = libm
 
     cpu = None
     if dist.rank == 0 and not args.no_cpu_baseline:

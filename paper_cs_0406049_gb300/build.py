@@ -25,6 +25,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsincos_gb300.so")
+CONTEXT_SRC = os.path.join(HERE, "context", "cuda_libm.cu")
+CONTEXT_LIB = os.path.join(HERE, "context", "libsincos_context.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
@@ -98,7 +100,29 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     return LIB
 
 
+def build_context(force: bool = False) -> str:
+    """The CUDA sincosf / __sincosf comparison kernels (benchmark context only),
+    compiled with nvcc's default floating-point flags."""
+    tag_file = CONTEXT_LIB + ".srctag"
+    with open(CONTEXT_SRC, "rb") as f:
+        tag = hashlib.sha1(f.read() + " ".join(ARCH).encode()).hexdigest()[:16]
+    if not force and os.path.exists(CONTEXT_LIB) and os.path.exists(tag_file):
+        with open(tag_file) as f:
+            if f.read().strip() == tag:
+                return CONTEXT_LIB
+    tmp = CONTEXT_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, CONTEXT_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on cuda_libm.cu:\n{r.stdout}{r.stderr}")
+    os.replace(tmp, CONTEXT_LIB)
+    with open(tag_file, "w") as f:
+        f.write(tag)
+    return CONTEXT_LIB
+
+
 if __name__ == "__main__":
     p = build(force="--force" in sys.argv, verbose=True,
               ptxas_verbose="--ptxas-verbose" in sys.argv)
     print(p)
+    print(build_context(force="--force" in sys.argv))
