@@ -332,6 +332,11 @@ const char *sincos_last_error(void);
  * previous call; the count is cleared by reading it.  Nonzero means a launch
  * stopped early and its outputs are incomplete.  Synchronizes the device. */
 uint32_t sincos_device_wait_timeouts(void);
+/* Self-test of the timeout path (the paper has no counterpart): one CTA waits
+ * on a barrier nothing ever completes, giving up after `spins` polls
+ * (1 .. 2^20) as the bulk kernels do; the next sincos_device_wait_timeouts()
+ * then reports one more timeout.  No fault, no trap: the device stays usable. */
+int sincos_selftest_wait_timeout(uint32_t spins, sincos_stream_t stream);
 /* Kernel launches this library has enqueued since load (all threads); a
  * graph replay counts the kernels in the graph. */
 uint64_t sincos_launch_count(void);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "sincos_strerror": (ctypes.c_char_p, [_INT]),
     "sincos_last_error": (ctypes.c_char_p, []),
     "sincos_device_wait_timeouts": (ctypes.c_uint32, []),
+    "sincos_selftest_wait_timeout": (_INT, [ctypes.c_uint32, _VP]),
     "sincos_launch_count": (ctypes.c_uint64, []),
     "sincos_version": (_INT, []),
 }

@@ -5,6 +5,7 @@
 #include <string>
 #include <unordered_map>
 
+#include "bulk.cuh"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -133,6 +134,21 @@ sincos_plan fit_plan(const void *kernel, const sincos_plan &plan, int *per_sm)
     return p;
 }
 
+// One CTA waits on an mbarrier that nothing ever arrives on, with the given
+// spin limit, exactly as the bulk kernels wait on their stages; the wait gives
+// up and counts a timeout.  Exercises the timeout path without a fault.
+__global__ void k_selftest_wait(unsigned spins)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&bar), 0u, spins))
+        atomicAdd(&g_bulk_wait_timeouts, 1u);
+}
+
 bool valid_dtype(int d) { return d == SINCOS_F32 || d == SINCOS_BF16 || d == SINCOS_F16; }
 bool valid_reduction(int r) { return r == SINCOS_RED_PLAIN || r == SINCOS_RED_COMPENSATED; }
 bool valid_coef(int c) { return c == SINCOS_COEF_NORMALIZED || c == SINCOS_COEF_DAGGER; }
@@ -211,7 +227,17 @@ uint32_t sincos_device_wait_timeouts(void)
 {
     return take_timeouts_forward_f32() + take_timeouts_forward_bf16() + take_timeouts_forward_f16() +
            take_timeouts_batched_f32() + take_timeouts_batched_bf16() + take_timeouts_batched_f16() +
-           take_timeouts_expi();
+           take_timeouts_expi() + take_bulk_wait_timeouts_here();
+}
+
+int sincos_selftest_wait_timeout(uint32_t spins, sincos_stream_t stream)
+{
+    if (spins == 0 || spins > (1u << 20)) return SINCOS_EINVAL;
+    const DeviceInfo *dev = nullptr;
+    const int rc = current_device(&dev);
+    if (rc != SINCOS_OK) return rc;
+    k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(spins);
+    return check_launch("wait self-test launch");
 }
 
 uint64_t sincos_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

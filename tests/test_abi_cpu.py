@@ -43,6 +43,11 @@ def test_binding_declares_nothing_extra():
     assert set(_lib.SIGNATURES) == set(declared_functions())
 
 
+def test_selftest_validation(lib):
+    assert lib.sincos_selftest_wait_timeout(0, None) == _lib.EINVAL
+    assert lib.sincos_selftest_wait_timeout((1 << 20) + 1, None) == _lib.EINVAL
+
+
 def test_status_strings(lib):
     for st in (0, -1, -2, -3, -4, -5):
         assert lib.sincos_strerror(st)
