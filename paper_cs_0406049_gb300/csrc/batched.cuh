@@ -277,6 +277,43 @@ __device__ __forceinline__ void tile_bulk_part(const TileWalk &w, int64_t t, int
 // never holds one of the two ring stages.
 constexpr int64_t kBulkMinAngles = kBulkChunk / 4;
 
+// Pairs of the E angles at element e of a staged input tile into the staged
+// output tiles (16-byte shared-memory accesses).
+template <int RED, int COEF, class OutT>
+__device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *co, int e)
+{
+    constexpr int E = Vec<OutT, 16>::E;
+    float in[E];
+#pragma unroll
+    for (int q = 0; q < E; q += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(xi + e + q);
+        in[q] = v.x;
+        in[q + 1] = v.y;
+        in[q + 2] = v.z;
+        in[q + 3] = v.w;
+    }
+    float sv[E], cv[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) pair<RED, COEF>(in[i], sv[i], cv[i]);
+    uint32_t ws[4], wc[4];
+    if constexpr (sizeof(OutT) == 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ws[i] = __float_as_uint(sv[i]);
+            wc[i] = __float_as_uint(cv[i]);
+        }
+    } else {
+        OutT *tag = nullptr;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ws[i] = pack2(tag, sv[2 * i], sv[2 * i + 1]);
+            wc[i] = pack2(tag, cv[2 * i], cv[2 * i + 1]);
+        }
+    }
+    *reinterpret_cast<uint4 *>(so + e) = make_uint4(ws[0], ws[1], ws[2], ws[3]);
+    *reinterpret_cast<uint4 *>(co + e) = make_uint4(wc[0], wc[1], wc[2], wc[3]);
+}
+
 // Thread 0: find the next ring-worthy tile at or after *tp (advancing the
 // producer walk) and start its bulk load into `dst`; false if none is left.
 template <class OutT>
@@ -389,37 +426,14 @@ k_batched_bulk(const sincos_seg *segs, const int64_t *lens, const int64_t *prefi
         const float *xi = xin + st * kBulkChunk;
         OutT *so = sout + b * kBulkChunk;
         OutT *co = cout + b * kBulkChunk;
+        if (mb == kBulkChunk) {           // a whole tile: fixed, fully unrolled trip count
+#pragma unroll
+            for (int j = 0; j < kBulkChunk / (NT * E); ++j)
+                bulk_tile_vec<RED, COEF, OutT>(xi, so, co, (j * NT + tid) * E);
+        } else {
 #pragma unroll 2
-        for (int64_t e = (int64_t)tid * E; e < mb; e += (int64_t)NT * E) {
-            float in[E];
-#pragma unroll
-            for (int q = 0; q < E; q += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(xi + e + q);
-                in[q] = v.x;
-                in[q + 1] = v.y;
-                in[q + 2] = v.z;
-                in[q + 3] = v.w;
-            }
-            float sv[E], cv[E];
-#pragma unroll
-            for (int i = 0; i < E; ++i) pair<RED, COEF>(in[i], sv[i], cv[i]);
-            uint32_t ws[4], wc[4];
-            if constexpr (sizeof(OutT) == 4) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    ws[i] = __float_as_uint(sv[i]);
-                    wc[i] = __float_as_uint(cv[i]);
-                }
-            } else {
-                OutT *tag = nullptr;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    ws[i] = pack2(tag, sv[2 * i], sv[2 * i + 1]);
-                    wc[i] = pack2(tag, cv[2 * i], cv[2 * i + 1]);
-                }
-            }
-            *reinterpret_cast<uint4 *>(so + e) = make_uint4(ws[0], ws[1], ws[2], ws[3]);
-            *reinterpret_cast<uint4 *>(co + e) = make_uint4(wc[0], wc[1], wc[2], wc[3]);
+            for (int64_t e = (int64_t)tid * E; e < mb; e += (int64_t)NT * E)
+                bulk_tile_vec<RED, COEF, OutT>(xi, so, co, (int)e);
         }
         for (int64_t i = v0 + mb + tid; i < end; i += NT) scalar_elem<RED, COEF>(xs, ss, cs, i);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
