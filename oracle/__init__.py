@@ -11,7 +11,9 @@ FP64 sine/cosine used to *state* errors; it is never a parity target.
 
 Parity status: every exported function is pinned by the CPU test suite
 (``tests/test_oracle_pins.py``, ``tests/test_oracle_mutations.py``); none is
-unpinned.
+unpinned.  ``doublings.py`` is a study model of the method with n doublings
+(no GPU counterpart), pinned bit for bit to this oracle at the paper's n = 2
+(``tests/test_doubling_study.py``).
 """
 from __future__ import annotations
 
