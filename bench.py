@@ -329,9 +329,18 @@ def cpu_baseline(x: np.ndarray) -> dict:
         used = oracle.sincos_mt(xs, s, c, threads=cores)
         reps += 1
     dt = time.perf_counter() - t0
+    # the same oracle on one thread, for the per-core rate
+    x1 = xs[: 1 << 24]
+    reps1, t1 = 0, time.perf_counter()
+    while reps1 < 1 or (time.perf_counter() - t1 < 2.0 and reps1 < 10):
+        oracle.sincos_mt(x1, s[: x1.size], c[: x1.size], threads=1)
+        reps1 += 1
+    dt1 = time.perf_counter() - t1
     return {"value": xs.size * reps / dt, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"first 2^26 angles of the {WORKLOAD} workload, {reps} passes, "
-                      f"{dt:.1f} s wall on {used} threads"}
+                      f"{dt:.1f} s wall on {used} threads",
+            "single_thread": {"value": x1.size * reps1 / dt1, "unit": UNIT,
+                              "sample": f"first 2^24 angles, {reps1} passes, {dt1:.1f} s"}}
 
 
 def cuda_libm_context(torch, x_np, x, s, c, dist, steps: int) -> dict:

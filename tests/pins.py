@@ -152,6 +152,44 @@ def pin_bruteforce(lib, ranges=((0.5, 1.0), (1.0, 2.0), (2.0, 4.0), (4.0, 8.0)))
         assert np.hypot(s - rs, c - rc).max() <= 7e-7, (lo, hi)
 
 
+def _bruteforce_bits(lib_cls, path, lo_bits, hi_bits):
+    """Worker of pin_bruteforce_small_angles: every positive binary32 whose bit
+    pattern is in [lo_bits, hi_bits), against FP64.  Returns the largest core
+    error, the largest excess of the plain total error over its bound, and the
+    largest compensated error."""
+    lib = lib_cls(path)
+    x = np.arange(lo_bits, hi_bits, dtype=np.int32).view(np.float32)
+    s, c = lib.sincos(x)
+    core = float(core_error(x, s, c).max())
+    rs, rc = np.sin(x.astype(np.float64)), np.cos(x.astype(np.float64))
+    excess = float((np.hypot(s - rs, c - rc) - reduction_bound(x)).max())
+    s, c = lib.sincos(x, reduction="compensated")
+    comp = float(np.hypot(s - rs, c - rc).max())
+    return core, excess, comp
+
+
+def pin_bruteforce_small_angles(lib, processes: int | None = None):
+    """Every binary32 in [0, 1/2), zero and subnormals included, one binade per
+    task over a spawned process pool: the same bounds as pin_bruteforce.  With
+    pin_bruteforce ([1/2, 8)) and pin_symmetry this covers every float in
+    [-pi, pi)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+
+    top = int(np.float32(0.5).view(np.int32))
+    step = 1 << 23                                  # one binade of bit patterns
+    tasks = [(b, min(b + step, top)) for b in range(0, top, step)]
+    workers = processes or min(8, len(os.sched_getaffinity(0)))
+    with ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+        futs = [ex.submit(_bruteforce_bits, type(lib), lib.path, lo, hi) for lo, hi in tasks]
+        results = [f.result() for f in futs]
+    for (lo, hi), (core, excess, comp) in zip(tasks, results):
+        where = (float(np.int32(lo).view(np.float32)), float(np.int32(hi).view(np.float32)))
+        assert core <= CORE_BOUND, (where, core)
+        assert excess <= CORE_BOUND, (where, excess)
+        assert comp <= 7e-7, (where, comp)
+
+
 # ----------------------------------------------------------------------------
 # Exact invariants.
 # ----------------------------------------------------------------------------
@@ -457,7 +495,8 @@ def pin_huygens_edges(lib):
 
 
 ALL_PINS = [
-    pin_e1_normalized, pin_e2_dagger, pin_drift_correction, pin_bruteforce, pin_symmetry,
+    pin_e1_normalized, pin_e2_dagger, pin_drift_correction, pin_bruteforce,
+    pin_bruteforce_small_angles, pin_symmetry,
     pin_periodicity, pin_exact_at_whole_turns, pin_quarter_turns, pin_ties_to_even,
     pin_special_values, pin_plain_reduction_bound, pin_compensated, pin_bf16_rounding,
     pin_f16_rounding, pin_16bit_outputs, pin_backward, pin_huygens_fp64, pin_huygens_airy,
