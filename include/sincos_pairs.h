@@ -175,16 +175,17 @@ typedef struct {
 } sincos_seg;
 
 /* The forward over `count` independent arrays in one launch pair (a tiny
- * prefix-sum kernel over the lengths, then one persistent kernel whose CTAs
+ * schedule kernel over the lengths, then one persistent kernel whose CTAs
  * each take a contiguous run of fixed-size tiles of the concatenated element
- * space).  Same per-element arithmetic as sincos_pairs_ex.
+ * space, the runs cut so that every CTA gets the same number of elements to
+ * within one tile).  Same per-element arithmetic as sincos_pairs_ex.
  *   segs  device array of `count` descriptors, read by the kernels.
  *   lens  device array of `count` int64 lengths; a negative length counts
  *         as 0.  Both arrays are read when the kernels run, so they may be
  *         filled by earlier work on the same stream.
  * No output may overlap another segment's output or any segment's angles
  * (not checked: the descriptors live on the device).
- * Scratch: the library keeps one small device buffer ((count+1) int64) per
+ * Scratch: the library keeps one small device buffer (count + 8195 int64) per
  * (device, stream) pair, allocated with cudaMalloc on the first call that
  * needs a larger one.  A call that would allocate while `stream` is being
  * captured returns SINCOS_ECAPTURE; make one uncaptured call first.
@@ -202,10 +203,11 @@ int sincos_batched_release(void);
  * must not risk the device-wide synchronization cudaMalloc/cudaFree can
  * trigger, or code under an allocation budget fixed at start-up cannot let
  * the library call cudaMalloc for scratch, as sincos_batched does on first
- * use.  This entry point allocates nothing: its tile-prefix scratch is a
- * fixed device array of SINCOS_NOALLOC_MAX_SEGMENTS + 1 int64 (512 KiB)
- * built into the library, present on every GPU that loads it until the
- * process exits.
+ * use.  This entry point allocates nothing: its schedule scratch (the
+ * tile prefix of up to SINCOS_NOALLOC_MAX_SEGMENTS arrays and the start of
+ * each CTA) is a fixed device array of SINCOS_NOALLOC_MAX_SEGMENTS + 8195
+ * int64 (about 576 KiB) built into the library, present on every GPU that
+ * loads it until the process exits.
  *   Arguments, layout, results and errors are those of sincos_batched_ex;
  *   count > SINCOS_NOALLOC_MAX_SEGMENTS returns SINCOS_EUNSUPPORTED before
  *   anything is enqueued.

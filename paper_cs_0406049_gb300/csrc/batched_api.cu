@@ -38,7 +38,8 @@ int validate(const sincos_seg *segs, const int64_t *lens, int count, int dtype, 
 
 }  // namespace
 
-// Device scratch of at least (count+1) int64 for `st` on the current device.
+// Device scratch of at least batched_scratch_elems(count) int64 for `st` on
+// the current device.
 // Grows (after synchronizing `st`, whose earlier batched work may still read
 // the old buffer) when too small; refuses to allocate while `st` is captured.
 int batched_scratch(cudaStream_t st, int count, int64_t **prefix)
@@ -46,7 +47,7 @@ int batched_scratch(cudaStream_t st, int count, int64_t **prefix)
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    const size_t need = sizeof(int64_t) * ((size_t)count + 1);
+    const size_t need = sizeof(int64_t) * batched_scratch_elems(count);
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     Scratch &sc = g_scratch[std::make_pair(dev, (uintptr_t)st)];
     if (sc.bytes < need) {
@@ -140,7 +141,7 @@ int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int
     sincos_graph g = new sincos_graph_s;
     g->device = dev->ordinal;
     cudaStream_t cap = nullptr;
-    cudaError_t e = cudaMalloc((void **)&g->prefix, sizeof(int64_t) * ((size_t)count + 1));
+    cudaError_t e = cudaMalloc((void **)&g->prefix, sizeof(int64_t) * batched_scratch_elems(count));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "graph create (scratch or stream)");

@@ -4,10 +4,10 @@
 namespace sincos_gb300 {
 
 int launch_batched_bf16(const sincos_seg *segs, const int64_t *lens, int count, int red, int coef,
-                        int64_t *prefix, const sincos_plan &plan, const DeviceInfo &dev,
+                        int64_t *sched, const sincos_plan &plan, const DeviceInfo &dev,
                         cudaStream_t st)
 {
-    return launch_batched_t<__nv_bfloat16>(segs, lens, count, red, coef, prefix, plan, dev, st);
+    return launch_batched_t<__nv_bfloat16>(segs, lens, count, red, coef, sched, plan, dev, st);
 }
 
 unsigned take_timeouts_batched_bf16() { return take_bulk_wait_timeouts_here(); }

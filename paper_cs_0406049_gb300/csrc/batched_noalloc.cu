@@ -23,10 +23,11 @@ namespace sincos_gb300 {
 
 namespace {
 
-// prefix[0 .. count] of the batched schedule (see batched.cu).  Every call
-// writes all the entries it later reads, so nothing needs clearing between
-// calls.
-__device__ __align__(256) int64_t g_noalloc_prefix[SINCOS_NOALLOC_MAX_SEGMENTS + 1];
+// The batched schedule (tile prefix of up to SINCOS_NOALLOC_MAX_SEGMENTS
+// segments, then the per-CTA starts; see batched.cuh).  Every call writes all
+// the entries it later reads, so nothing needs clearing between calls.
+__device__ __align__(256) int64_t g_noalloc_prefix[SINCOS_NOALLOC_MAX_SEGMENTS + 1 +
+                                                   2 * (kMaxBatchedCtas + 1)];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;

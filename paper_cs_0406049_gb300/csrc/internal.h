@@ -77,10 +77,19 @@ int launch_huygens(const float *px, const float *py, const float *pz, int64_t m,
 int launch_backward(const float *gs, const float *gc, const float *s, const float *c, float *gx,
                     int64_t n, bool in_place, const sincos_plan &plan, const DeviceInfo &dev,
                     cudaStream_t st);
-// Batched: prefix kernel over lens into `prefix` ((count+1) int64 of device
-// scratch), then the persistent tile kernel.
+// Batched schedule scratch, int64 of device memory: prefix[0 .. count] (tiles
+// before each segment), then first_tile[0 .. G] and first_seg[0 .. G] for the
+// G <= kMaxBatchedCtas CTAs of the tile kernel.
+constexpr int kMaxBatchedCtas = 4096;
+inline size_t batched_scratch_elems(int count)
+{
+    return (size_t)count + 1 + 2 * ((size_t)kMaxBatchedCtas + 1);
+}
+
+// Batched: schedule kernel over lens into `sched` (batched_scratch_elems(count)
+// int64 of device scratch), then the persistent tile kernel.
 int launch_batched(const sincos_seg *segs, const int64_t *lens, int count, int dtype, int red,
-                   int coef, int64_t *prefix, const sincos_plan &plan, const DeviceInfo &dev,
+                   int coef, int64_t *sched, const sincos_plan &plan, const DeviceInfo &dev,
                    cudaStream_t st);
 
 

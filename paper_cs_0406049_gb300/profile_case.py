@@ -67,14 +67,19 @@ def main(argv=None):
         use_plan("backward", "f32", n)
         run = lambda: api.sincos_backward(gs, gc, s, c, gx)
     else:
-        # 4096 segments of pseudo-random lengths packed into the n angles
-        lens = torch.randint(1, 2 * (n // 4096), (4096,), generator=g, device="cuda")
-        lens = (lens * n // int(lens.sum())).clamp(min=1).cpu()
-        offs = torch.cumsum(lens, 0) - lens
-        keep = offs + lens <= n
-        s = torch.empty_like(x)
-        c = torch.empty_like(x)
-        segs, lens_t = api.segments(x, s, c, offs[keep].numpy(), lens[keep].numpy())
+        # 4096 arrays packed back to back with the batching workload's
+        # log-uniform lengths, clamp(round(2^(mU)), 1, 2^m) with m = log2n - 8
+        # (m = 20 at log2n = 28 gives that workload's lengths exactly)
+        import numpy as np
+        from . import workloads
+        lens = workloads.batch_lengths(4096, max(1, a.log2n - 8), np.random.default_rng(3))
+        offs = np.concatenate([[0], np.cumsum(lens)[:-1]])
+        total = int(lens.sum())
+        xb = (torch.rand(total, device="cuda", generator=g) * 200.0 - 100.0).contiguous()
+        del x
+        s = torch.empty_like(xb)
+        c = torch.empty_like(xb)
+        segs, lens_t = api.segments(xb, s, c, offs, lens)
         use_plan("batched", "f32", lens_t.numel())
         run = lambda: api.sincos_batched(segs, lens_t)
     for _ in range(a.launches):

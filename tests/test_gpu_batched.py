@@ -54,6 +54,33 @@ def test_edge_lengths(cuda_lib, dtype, red, coef, path):
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
+def test_all_lengths_empty(cuda_lib, path):
+    """No elements at all: every CTA's run is empty and nothing is written."""
+    lens = [0, -4, 0, -1]
+    x = mixed_angles(64, 3)
+    xt = torch.from_numpy(x).cuda()
+    s = torch.full_like(xt, 7.0)
+    c = torch.full_like(xt, 7.0)
+    segs, lens_t = api.segments(xt, s, c, [0, 8, 16, 24], lens)
+    with forced_plan("batched", "f32", PATHS[path]):
+        api.sincos_batched(segs, lens_t)
+    torch.cuda.synchronize()
+    assert torch.all(s == 7.0) and torch.all(c == 7.0)
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_one_long_segment_then_short_ones(cuda_lib, path):
+    """Most CTA boundaries fall inside the first segment (at its head, inside
+    tiles, at its end); the short segments after it share the last runs."""
+    lens = [3 * (1 << 20) + 13] + [1, 0, 5, 33, 4097, 2, 0, 9000, 1, 1]
+    x, xt, s, c, offs = packed(lens, "f32", seed=4)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    with forced_plan("batched", "f32", PATHS[path]):
+        api.sincos_batched(segs, lens_t)
+    check_all(x, s, c, "f32", "plain", "normalized", f"long then short {path}")
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
 def test_negative_and_empty_lengths(cuda_lib, path):
     lens = [5, -3, 0, 9, -100, 1, 20000, -1]
     x, xt, s, c, offs = packed(lens, "f32", seed=2)
