@@ -178,3 +178,46 @@ def test_batching_workload_full_size(cuda_lib):
     torch.cuda.synchronize()
     assert torch.equal(s.view(torch.int32), s3.view(torch.int32))
     assert torch.equal(c.view(torch.int32), c3.view(torch.int32))
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_gaps_between_arrays_stay_untouched(cuda_lib, path, dtype):
+    """Arrays placed in one buffer with sentinel-filled gaps of 1-40 elements
+    between them (and 64 before and after): every gap element is unchanged
+    after the call, every array element matches the oracle."""
+    rng = np.random.default_rng(21)
+    lens = [int(v) for v in rng.choice([1, 3, 7, 31, 100, 4097, 8191, 8192, 8195, 20000, 70001],
+                                       200)]
+    gaps = rng.integers(1, 41, len(lens))
+    offs, pos = [], 64
+    for n, g in zip(lens, gaps):
+        offs.append(pos)
+        pos += n + int(g)
+    total = pos + 64
+    x = mixed_angles(total, 8)
+    xt = torch.from_numpy(x).cuda()
+    if dtype == "f32":
+        fill = torch.tensor(np.array([0x7fa5a5a5], np.uint32).view(np.int32)[0]).item()
+        s = torch.full((total,), fill, dtype=torch.int32, device="cuda").view(torch.float32)
+        c = s.clone()
+        sent = np.uint32(0x7fa5a5a5)
+    else:
+        s = torch.full((total,), 0x7da5, dtype=torch.int16, device="cuda").view(torch.bfloat16)
+        c = s.clone()
+        sent = np.uint16(0x7da5)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    with forced_plan("batched", dtype, PATHS[path]):
+        api.sincos_batched(segs, lens_t, dtype)
+    torch.cuda.synchronize()
+    inside = np.zeros(total, bool)
+    for o, n in zip(offs, lens):
+        inside[o:o + n] = True
+    for name, t in (("s", s), ("c", c)):
+        raw = as_np(t)
+        raw = raw.view(np.uint32) if dtype == "f32" else raw
+        assert np.all(raw[~inside] == sent), f"{path} {dtype}: {name} written outside the arrays"
+    xs = np.concatenate([x[o:o + n] for o, n in zip(offs, lens)])
+    sel = np.concatenate([np.arange(o, o + n) for o, n in zip(offs, lens)])
+    check_all(xs, s[torch.from_numpy(sel).cuda()], c[torch.from_numpy(sel).cuda()], dtype,
+              "plain", "normalized", f"gaps {path} {dtype}")
