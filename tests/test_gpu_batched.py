@@ -221,3 +221,21 @@ def test_gaps_between_arrays_stay_untouched(cuda_lib, path, dtype):
     sel = np.concatenate([np.arange(o, o + n) for o, n in zip(offs, lens)])
     check_all(xs, s[torch.from_numpy(sel).cuda()], c[torch.from_numpy(sel).cuda()], dtype,
               "plain", "normalized", f"gaps {path} {dtype}")
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+@pytest.mark.parametrize("count", [5000, 20000, 65536])
+def test_many_arrays(cuda_lib, path, count):
+    """More arrays than the ring kernel's threads hold in one batch of
+    metadata each (its prologue then reloads them for the second pass), with
+    empty arrays, short ones and a few long ones, against the oracle."""
+    rng = np.random.default_rng(count)
+    lens = rng.integers(0, 40, count)
+    lens[rng.integers(0, count, 12)] = rng.integers(8000, 60000, 12)
+    lens[::53] = 0
+    x, xt, s, c, offs = packed(lens, "f32", seed=5)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    with forced_plan("batched", "f32", PATHS[path]):
+        api.sincos_batched(segs, lens_t)
+    check_all(x, s, c, "f32", "plain", "normalized", f"{count} arrays {path}")
+    assert api.sincos_device_wait_timeouts() == 0
