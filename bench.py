@@ -214,6 +214,20 @@ def profiled_traffic():
     return float(m.group(1))
 
 
+def vendor_peak(torch, achieved_gbs: float) -> dict:
+    """The nominal HBM bandwidth from the device's attributes (peak memory
+    clock x bus width x 2 transfers per clock), reported beside the measured
+    copy peak; empty if this PyTorch does not expose the attributes."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    khz = getattr(props, "memory_clock_rate", 0) or 0
+    bits = getattr(props, "memory_bus_width", 0) or 0
+    if not khz or not bits:
+        return {}
+    gbs = khz * 1e3 * bits / 8 * 2 / 1e9
+    return {"peak_vendor": gbs, "frac_vendor": achieved_gbs / gbs,
+            "peak_vendor_kind": f"memory clock {khz / 1e3:.0f} MHz x {bits}-bit bus x 2"}
+
+
 def aggregate_value(world: int, n_per_rank: int, steps: int, max_ms: float) -> float:
     """Whole-job pairs/s: every rank computed n_per_rank pairs per step; the
     slowest rank's time for all steps bounds the job."""
@@ -621,7 +635,8 @@ def run_ours(args, dist: Dist):
                                     if plan["vec_bytes"] == 0 else
                                     f"k_forward<float, plain, normalized, {plan['unroll']}, "
                                     f"{plan['vec_bytes']}>"),
-                         "bytes_per_launch": BYTES_PER_PAIR * n, "kernel_ms": kernel_ms},
+                         "bytes_per_launch": BYTES_PER_PAIR * n, "kernel_ms": kernel_ms,
+                         **vendor_peak(torch, achieved)},
             "errors_vs_fp64": err,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -6,6 +6,7 @@
 #include <unordered_map>
 
 #include "bulk.cuh"
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -162,6 +163,7 @@ extern "C" {
 int sincos_pairs_ex(const float *x, void *s, void *c, int64_t n, int out_dtype, int reduction,
                     int coef, sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_pairs_ex");
     if (n < 0 || !valid_dtype(out_dtype) || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
@@ -191,6 +193,7 @@ int sincos_pairs(const float *x, float *s, float *c, int64_t n, sincos_stream_t 
 int sincos_backward(const float *gs, const float *gc, const float *s, const float *c, float *gx,
                     int64_t n, sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_backward");
     if (n < 0) return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
     if (!gx || ((gs || gc) && (!s || !c))) return SINCOS_EINVAL;

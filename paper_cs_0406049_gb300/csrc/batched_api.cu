@@ -4,6 +4,7 @@
 #include <mutex>
 #include <utility>
 
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -88,6 +89,7 @@ extern "C" {
 int sincos_batched_ex(const sincos_seg *segs, const int64_t *lens, int count, int out_dtype,
                       int reduction, int coef, sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_batched_ex");
     int rc = validate(segs, lens, count, out_dtype, reduction, coef);
     if (rc != SINCOS_OK || count == 0) return rc;
     const DeviceInfo *dev = nullptr;
@@ -129,6 +131,7 @@ int sincos_batched_release(void)
 int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int count,
                                 int out_dtype, int reduction, int coef, sincos_graph *out)
 {
+    SINCOS_TRACE("sincos_batched_graph_create");
     if (!out) return SINCOS_EINVAL;
     *out = nullptr;
     int rc = validate(segs, lens, count, out_dtype, reduction, coef);
@@ -177,6 +180,7 @@ int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int
 
 int sincos_batched_graph_launch(sincos_graph g, sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_batched_graph_launch");
     if (!g || !g->exec) return SINCOS_EINVAL;
     const cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");

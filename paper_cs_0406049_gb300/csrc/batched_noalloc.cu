@@ -17,6 +17,7 @@
 // cached.
 #include <mutex>
 
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -59,6 +60,7 @@ extern "C" int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *len
                                       int out_dtype, int reduction, int coef,
                                       sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_batched_noalloc");
     if (count < 0 || !valid_dtype(out_dtype) || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
     if (count == 0) return SINCOS_OK;

@@ -10,6 +10,7 @@
 // of bulk.cuh; each chunk's 64 KB of output leaves in one bulk store.
 #include "bulk.cuh"
 #include "core.cuh"
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -288,6 +289,7 @@ using namespace sincos_gb300;
 extern "C" int sincos_expi(const float *x, float *z, int64_t n, int reduction, int coef,
                            sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_expi");
     if (n < 0 || !valid_reduction(reduction) || !valid_coef(coef)) return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
     if (!x || !z) return SINCOS_EINVAL;

@@ -5,6 +5,7 @@
 // parallel).  The device side uses only the caller's workspace.
 #include <mutex>
 
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -69,6 +70,7 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
                       int reduction, int coef, void *dev_ws, size_t ws_bytes,
                       sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_pairs_host");
     if (n < 0 || !valid_dtype(out_dtype) || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;

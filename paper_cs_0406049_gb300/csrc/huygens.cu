@@ -17,6 +17,7 @@
 // the same time (a broadcast), so each source costs two shared loads per P
 // terms of about 40 FP32 operations each.  The kernel is FP32-pipe bound.
 #include "core.cuh"
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -157,6 +158,7 @@ extern "C" int sincos_huygens(const float *px, const float *py, const float *pz,
                               const float *ar, const float *ai, int64_t n, float k,
                               int reduction, float *u, sincos_stream_t stream)
 {
+    SINCOS_TRACE("sincos_huygens");
     int rc = huygens_check(px, py, pz, m, qx, qy, qz, ar, ai, n, reduction, u);
     if (rc != 1) return rc;
     const DeviceInfo *dev = nullptr;

@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "trace.h"
 #include "internal.h"
 
 namespace sincos_gb300 {
@@ -291,6 +292,7 @@ int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan)
 int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_dtype,
                           int reduction, int coef, sincos_stream_t stream, sincos_plan *best)
 {
+    SINCOS_TRACE("sincos_autotune_pairs");
     if (n <= 0 || !x || !s || !c || !valid_dtype(out_dtype) || !valid_reduction(reduction) ||
         !valid_coef(coef))
         return SINCOS_EINVAL;
@@ -313,6 +315,7 @@ int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_d
 int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int coef,
                          sincos_stream_t stream, sincos_plan *best)
 {
+    SINCOS_TRACE("sincos_autotune_expi");
     if (n <= 0 || !x || !z || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
     const uintptr_t x0 = (uintptr_t)x, z0 = (uintptr_t)z;
@@ -334,6 +337,7 @@ int sincos_autotune_huygens(const float *px, const float *py, const float *pz, i
                             const float *ai, int64_t n, float k, int reduction, float *u,
                             sincos_stream_t stream, sincos_plan *best)
 {
+    SINCOS_TRACE("sincos_autotune_huygens");
     if (m <= 0 || n < 0 || !px || !py || !pz || !u || !valid_reduction(reduction))
         return SINCOS_EINVAL;
     if (n > 0 && (!qx || !qy || !qz || !ar || !ai)) return SINCOS_EINVAL;
@@ -353,6 +357,7 @@ int sincos_autotune_huygens(const float *px, const float *py, const float *pz, i
 int sincos_autotune_backward(const float *gs, const float *gc, const float *s, const float *c,
                              float *gx, int64_t n, sincos_stream_t stream, sincos_plan *best)
 {
+    SINCOS_TRACE("sincos_autotune_backward");
     if (n <= 0 || !gx || !s || !c) return SINCOS_EINVAL;
     for (const float *in : {gs, gc, s, c})
         if (in && (uintptr_t)in < (uintptr_t)(gx + n) && (uintptr_t)gx < (uintptr_t)(in + n))
@@ -373,6 +378,7 @@ int sincos_autotune_batched(const sincos_seg *segs, const int64_t *lens, int cou
                             int out_dtype, int reduction, int coef, sincos_stream_t stream,
                             sincos_plan *best)
 {
+    SINCOS_TRACE("sincos_autotune_batched");
     if (count <= 0 || !segs || !lens || !valid_dtype(out_dtype) || !valid_reduction(reduction) ||
         !valid_coef(coef))
         return SINCOS_EINVAL;
