@@ -214,13 +214,37 @@ def profiled_traffic():
     return float(m.group(1))
 
 
+def cudart_memory_attributes(dev: int):
+    """(peak memory clock in kHz, bus width in bits) from cudaDeviceGetAttribute
+    through the CUDA runtime already loaded by PyTorch; (0, 0) if unavailable."""
+    import ctypes
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+        except OSError:
+            continue
+        vals = []
+        for attr in (36, 37):      # cudaDevAttrMemoryClockRate, cudaDevAttrGlobalMemoryBusWidth
+            v = ctypes.c_int(0)
+            if rt.cudaDeviceGetAttribute(ctypes.byref(v), ctypes.c_int(attr), ctypes.c_int(dev)):
+                vals = []
+                break
+            vals.append(v.value)
+        if len(vals) == 2:
+            return vals[0], vals[1]
+    return 0, 0
+
+
 def vendor_peak(torch, achieved_gbs: float) -> dict:
     """The nominal HBM bandwidth from the device's attributes (peak memory
     clock x bus width x 2 transfers per clock), reported beside the measured
     copy peak; empty if this PyTorch does not expose the attributes."""
-    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
     khz = getattr(props, "memory_clock_rate", 0) or 0
     bits = getattr(props, "memory_bus_width", 0) or 0
+    if not khz or not bits:
+        khz, bits = cudart_memory_attributes(dev)
     if not khz or not bits:
         return {}
     gbs = khz * 1e3 * bits / 8 * 2 / 1e9
