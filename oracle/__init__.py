@@ -122,7 +122,10 @@ class OracleLib:
 
     def sincos_mt(self, x, s, c, reduction: str = "plain", coef: str = "normalized",
                   threads: int = 1) -> int:
-        """Threaded binary32 forward into caller arrays (timing only); returns threads used."""
+        """Threaded binary32 forward into caller arrays: ``oracle_sincos_f32`` on
+        contiguous sub-ranges, one per thread, so the results are those of
+        ``sincos``.  Used for the CPU timing and the exhaustive GPU comparison.
+        Returns the number of threads used."""
         for a in (x, s, c):
             assert a.dtype == np.float32 and a.flags.c_contiguous
         return self._lib.oracle_sincos_f32_mt(
