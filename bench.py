@@ -418,15 +418,17 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     rng = np.random.default_rng(0)
     idx = torch.from_numpy(rng.integers(0, x.size, 1 << 20)).cuda()
     prec = {}
-    for name, dt, red in (("f32_plain", torch.float32, "plain"),
-                          ("f32_compensated", torch.float32, "compensated"),
-                          ("bf16_compensated", torch.bfloat16, "compensated"),
-                          ("f16_compensated", torch.float16, "compensated")):
+    for name, dt, red, coef in (("f32_plain", torch.float32, "plain", "normalized"),
+                                ("f32_compensated", torch.float32, "compensated", "normalized"),
+                                ("f32_plain_dagger", torch.float32, "plain", "dagger"),
+                                ("bf16_compensated", torch.bfloat16, "compensated", "normalized"),
+                                ("f16_compensated", torch.float16, "compensated", "normalized")):
         s = torch.empty(x.size, dtype=dt, device="cuda")
         c = torch.empty_like(s)
         if autotune:
-            api.sincos_autotune_pairs(xt, s, c, red)
-        total, per, _ = time_loop(torch, lambda: api.sincos_pairs_ex(xt, s, c, red), k, 3, dist)
+            api.sincos_autotune_pairs(xt, s, c, red, coef)
+        total, per, _ = time_loop(torch, lambda: api.sincos_pairs_ex(xt, s, c, red, coef), k, 3,
+                                  dist)
         bytes_ = x.size * (4 + 2 * s.element_size())
         ms = statistics.mean(per)
         err = fp64_errors(x[idx.cpu().numpy()], s[idx].float().cpu().numpy().astype(np.float64),
