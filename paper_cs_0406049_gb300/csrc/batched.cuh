@@ -446,98 +446,133 @@ struct RingRun {
     int64_t seg_a, k_a, seg_b, k_b;
 };
 
-// Work of a segment in the ring schedule: its angles plus kRingTileCost per
-// tile; also its tile count and grid start.
-template <class OutT>
-__device__ __forceinline__ void ring_seg_cost(const sincos_seg &d, int64_t len, int64_t *w,
-                                              int64_t *nt, int *h)
+// Chunks of blockDim.x segments that ring_run sums at a time, and the chunk
+// totals it keeps in shared memory for its second pass.
+constexpr int kRunBatch = 8;
+constexpr int kRunChunks = 128;
+
+// Work of a segment of length len in the ring schedule: its angles plus
+// kRingTileCost per tile, counting ceil(len / T) tiles.  (Its exact tile count
+// also depends on the grid start; the schedule only needs a cost that every
+// CTA computes the same way from the lengths alone.)
+__device__ __forceinline__ int64_t ring_len_cost(int64_t len)
 {
     const int64_t ne = len > 0 ? len : 0;
-    *h = seg_head<OutT, 16>(d);
-    *nt = seg_tiles(ne, *h, kBulkChunk);
-    *w = ne + kRingTileCost * *nt;
+    return ne + kRingTileCost * ((ne + kBulkChunk - 1) / kBulkChunk);
 }
 
-// Segments a thread of ring_run loads at a time.
-constexpr int kRunBatch = 8;
-
-// Costs, tile counts and grid starts of segments [j0, min(j0 + kRunBatch, i1)),
-// all loads issued before any is used.
-template <class OutT>
-__device__ __forceinline__ void ring_load_batch(const sincos_seg *segs, const int64_t *lens,
-                                                int j0, int i1, int64_t *bw, int64_t *bnt,
-                                                int *bh)
+// Work of the segments of chunks [c0, c0 + kRunBatch) that belong to this
+// thread (segment (c0 + q) * P + tid in slot q); consecutive threads read
+// consecutive lengths, so the loads coalesce.
+__device__ __forceinline__ void ring_load_costs(const int64_t *lens, int count, int c0,
+                                                int64_t *bw)
 {
-    sincos_seg d[kRunBatch];
+    const int64_t P = blockDim.x;
     int64_t len[kRunBatch];
 #pragma unroll
     for (int q = 0; q < kRunBatch; ++q) {
-        if (j0 + q < i1) {
-            d[q] = segs[j0 + q];
-            len[q] = lens[j0 + q];
-        }
+        const int64_t i = (c0 + q) * P + threadIdx.x;
+        len[q] = i < count ? lens[i] : 0;
     }
 #pragma unroll
+    for (int q = 0; q < kRunBatch; ++q) bw[q] = ring_len_cost(len[q]);
+}
+
+// Sums over the CTA of v[0 .. kRunBatch), into tot[] (shared, kRunBatch).
+__device__ __forceinline__ void cta_sums(const int64_t *v, int64_t (*red)[32], int64_t *tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
     for (int q = 0; q < kRunBatch; ++q) {
-        bw[q] = 0;
-        bnt[q] = 0;
-        bh[q] = -1;
-        if (j0 + q < i1) ring_seg_cost<OutT>(d[q], len[q], &bw[q], &bnt[q], &bh[q]);
+        int64_t x = v[q];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+        if (lane == 0) red[q][warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < kRunBatch; ++q) {
+            int64_t x = lane < nwarps ? red[q][lane] : 0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+            if (lane == 0) tot[q] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Locate work position `at` inside chunk c whose work starts at `base`: a CTA
+// scan of the chunk's costs; the thread whose segment holds the position
+// writes (segment, first tile starting at or after it) to *seg, *k.
+template <class OutT>
+__device__ __forceinline__ void ring_locate(const sincos_seg *segs, const int64_t *lens,
+                                            int count, int c, int64_t base, int64_t at,
+                                            int64_t *seg, int64_t *k, int64_t *wa, int64_t *wb)
+{
+    const int64_t i = (int64_t)c * blockDim.x + threadIdx.x;
+    const int64_t len = i < count ? (lens[i] > 0 ? lens[i] : 0) : 0;
+    const int64_t w = ring_len_cost(len);
+    int64_t incl = w, zero = 0, t1 = 0, t2 = 0;
+    cta_scan2(incl, zero, wa, wb, &t1, &t2);
+    const int64_t from = base + incl - w;
+    if (w > 0 && at >= from && at < from + w) {
+        const int h = seg_head<OutT, 16>(segs[i]);
+        *seg = i;
+        *k = first_tile_from(at - from, h, kBulkChunk, seg_tiles(len, h, kBulkChunk), 1,
+                             kRingTileCost);
     }
 }
 
-// The CTA computes its own run, with all its threads: the batch's work W is
-// summed (each thread a contiguous block of segments, then one CTA scan), and
-// CTA b of G takes the tiles from the first one starting at or after work
-// floor(W b / G) to the first one starting at or after floor(W (b+1) / G).
-// CTAs b and b + 1 compute the same boundary, so the runs tile the batch.
-// Each thread loads its segments' metadata kRunBatch at a time with all loads
-// in flight together, and keeps the costs for the second pass when its block
-// is one batch.
+// The CTA computes its own run, with all its threads.  The batch's work W is
+// summed over the lengths; CTA b of G then takes the tiles from the first one
+// starting at or after work floor(W b / G) to the first one starting at or
+// after floor(W (b+1) / G).  CTAs b and b + 1 compute the same boundary, so
+// the runs tile the batch.  Lengths are read in chunks of blockDim.x,
+// consecutive threads on consecutive segments; the chunk totals stay in shared
+// memory (up to kRunChunks chunks, else they are summed again), and only the
+// chunks holding the two boundaries are scanned.
 template <class OutT>
 __device__ __forceinline__ void ring_run(const sincos_seg *segs, const int64_t *lens, int count,
-                                         RingRun *run, int64_t *wa, int64_t *wb)
+                                         RingRun *run, int64_t *wa, int64_t *wb,
+                                         int64_t (*red)[32], int64_t *tot, int64_t *ctot)
 {
-    const int m = (count + (int)blockDim.x - 1) / (int)blockDim.x;
-    const int i0 = (int)threadIdx.x * m;
-    const int i1 = count < i0 + m ? count : i0 + m;
-    int64_t bw[kRunBatch], bnt[kRunBatch];
-    int bh[kRunBatch];
-    int64_t mine = 0;
-    for (int j0 = i0; j0 < i1; j0 += kRunBatch) {
-        ring_load_batch<OutT>(segs, lens, j0, i1, bw, bnt, bh);
-#pragma unroll
-        for (int q = 0; q < kRunBatch; ++q) mine += bw[q];
-    }
-    int64_t incl = mine, zero = 0, all = 0, unused = 0;
+    const int P = (int)blockDim.x;
+    const int nchunks = (count + P - 1) / P;
+    int64_t bw[kRunBatch];
     if (threadIdx.x == 0) {
         run->seg_a = run->seg_b = count;
         run->k_a = run->k_b = 0;
     }
-    cta_scan2(incl, zero, wa, wb, &all, &unused);
+    int64_t all = 0;
+    for (int c0 = 0; c0 < nchunks; c0 += kRunBatch) {
+        ring_load_costs(lens, count, c0, bw);
+        cta_sums(bw, red, tot);
+#pragma unroll
+        for (int q = 0; q < kRunBatch; ++q) {
+            if (threadIdx.x == 0 && c0 + q < kRunChunks) ctot[c0 + q] = tot[q];
+            all += tot[q];
+        }
+    }
+    __syncthreads();
     const int64_t lo = all * (int64_t)blockIdx.x / gridDim.x;
     const int64_t hi = all * ((int64_t)blockIdx.x + 1) / gridDim.x;
-    int64_t at = incl - mine;
-    if (mine > 0 && ((lo >= at && lo < at + mine) || (hi >= at && hi < at + mine))) {
-        for (int j0 = i0; j0 < i1; j0 += kRunBatch) {
-            if (m > kRunBatch) ring_load_batch<OutT>(segs, lens, j0, i1, bw, bnt, bh);
-#pragma unroll
-            for (int q = 0; q < kRunBatch; ++q) {
-                const int64_t w = bw[q];
-                if (w > 0) {
-                    if (lo >= at && lo < at + w) {
-                        run->seg_a = j0 + q;
-                        run->k_a = first_tile_from(lo - at, bh[q], kBulkChunk, bnt[q], 1,
-                                                   kRingTileCost);
-                    }
-                    if (hi >= at && hi < at + w) {
-                        run->seg_b = j0 + q;
-                        run->k_b = first_tile_from(hi - at, bh[q], kBulkChunk, bnt[q], 1,
-                                                   kRingTileCost);
-                    }
-                }
-                at += w;
-            }
+    int64_t base = 0;
+    for (int c0 = 0; c0 < nchunks && base <= hi; c0 += kRunBatch) {
+        if (nchunks > kRunChunks) {                  // totals not kept: sum this batch again
+            ring_load_costs(lens, count, c0, bw);
+            cta_sums(bw, red, tot);
+        }
+        for (int q = 0; q < kRunBatch && c0 + q < nchunks; ++q) {
+            const int64_t ct = nchunks > kRunChunks ? tot[q] : ctot[c0 + q];
+            if (lo >= base && lo < base + ct)        // uniform over the CTA
+                ring_locate<OutT>(segs, lens, count, c0 + q, base, lo, &run->seg_a, &run->k_a,
+                                  wa, wb);
+            if (hi >= base && hi < base + ct)
+                ring_locate<OutT>(segs, lens, count, c0 + q, base, hi, &run->seg_b, &run->k_b,
+                                  wa, wb);
+            base += ct;
         }
     }
     __syncthreads();
@@ -712,8 +747,9 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
     __shared__ int give_up;
     __shared__ RingRun run;
     __shared__ int64_t wa[32], wb[32];
+    __shared__ int64_t red[kRunBatch][32], tot[kRunBatch], ctot[kRunChunks];
 
-    ring_run<OutT>(segs, lens, count, &run, wa, wb);
+    ring_run<OutT>(segs, lens, count, &run, wa, wb, red, tot, ctot);
     const int tid = threadIdx.x;
     if (tid == 0) {
         give_up = 0;
