@@ -174,20 +174,24 @@ typedef struct {
     void *c;
 } sincos_seg;
 
-/* The forward over `count` independent arrays in one launch pair (a tiny
- * schedule kernel over the lengths, then one persistent kernel whose CTAs
- * each take a contiguous run of fixed-size tiles of the concatenated element
- * space, the runs cut so that every CTA gets the same number of elements to
- * within one tile).  Same per-element arithmetic as sincos_pairs_ex.
+/* The forward over `count` independent arrays: the method of Sec.
+ * Methodology and Fig. 1 applied to each array (batching itself is not in
+ * the paper).  Same per-element arithmetic as sincos_pairs_ex.  With the default plan for binary32 outputs this is one
+ * persistent launch.  Each CTA derives its own contiguous run of the
+ * concatenated element space from the lengths (equal work per CTA to within
+ * one 8192-angle tile), then streams it through a TMA-staged ring.  With a
+ * register plan (the default for 16-bit outputs) it is two launches: a small
+ * schedule kernel over the lengths into the scratch below, then the tile
+ * kernel.
  *   segs  device array of `count` descriptors, read by the kernels.
  *   lens  device array of `count` int64 lengths; a negative length counts
  *         as 0.  Both arrays are read when the kernels run, so they may be
  *         filled by earlier work on the same stream.
  * No output may overlap another segment's output or any segment's angles
  * (not checked: the descriptors live on the device).
- * Scratch: the library keeps one small device buffer (count + 8195 int64) per
- * (device, stream) pair, allocated with cudaMalloc on the first call that
- * needs a larger one.  A call that would allocate while `stream` is being
+ * Scratch (used by register plans): the library keeps one small device
+ * buffer (count + 8195 int64) per (device, stream) pair, allocated with
+ * cudaMalloc on the first call that needs a larger one.  A call that would allocate while `stream` is being
  * captured returns SINCOS_ECAPTURE; make one uncaptured call first.
  * sincos_batched_release() frees all such buffers (call it only when no
  * batched work is in flight). */
