@@ -96,12 +96,15 @@ int sincos_batched_ex(const sincos_seg *segs, const int64_t *lens, int count, in
     rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t *prefix = nullptr;
-    rc = batched_scratch(st, count, &prefix);
-    if (rc != SINCOS_OK) return rc;
     // Batched plans are keyed by the segment count (the lengths live on the
-    // device and are not read back).
+    // device and are not read back).  Only register plans use the schedule
+    // scratch; the ring kernel schedules itself.
     const sincos_plan plan = plan_for(*dev, SINCOS_OP_BATCHED, out_dtype, count);
+    int64_t *prefix = nullptr;
+    if (plan_vec_bytes(plan) != 0) {
+        rc = batched_scratch(st, count, &prefix);
+        if (rc != SINCOS_OK) return rc;
+    }
     return launch_batched(segs, lens, count, out_dtype, reduction, coef, prefix, plan, *dev, st);
 }
 
@@ -144,7 +147,10 @@ int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int
     sincos_graph g = new sincos_graph_s;
     g->device = dev->ordinal;
     cudaStream_t cap = nullptr;
-    cudaError_t e = cudaMalloc((void **)&g->prefix, sizeof(int64_t) * batched_scratch_elems(count));
+    const sincos_plan plan = plan_for(*dev, SINCOS_OP_BATCHED, out_dtype, count);
+    cudaError_t e = cudaSuccess;
+    if (plan_vec_bytes(plan) != 0)      // the schedule scratch of register plans
+        e = cudaMalloc((void **)&g->prefix, sizeof(int64_t) * batched_scratch_elems(count));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         rc = cuda_fail(e, "graph create (scratch or stream)");
@@ -152,7 +158,6 @@ int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int
         if (cap) cudaStreamDestroy(cap);
         return rc;
     }
-    const sincos_plan plan = plan_for(*dev, SINCOS_OP_BATCHED, out_dtype, count);
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         rc = launch_batched(segs, lens, count, out_dtype, reduction, coef, g->prefix, plan, *dev,

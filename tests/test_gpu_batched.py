@@ -239,3 +239,25 @@ def test_many_arrays(cuda_lib, path, count):
         api.sincos_batched(segs, lens_t)
     check_all(x, s, c, "f32", "plain", "normalized", f"{count} arrays {path}")
     assert api.sincos_device_wait_timeouts() == 0
+
+
+def test_ring_plan_captures_without_a_prior_call(cuda_lib):
+    """The ring kernel needs no scratch, so a binary32 batch can be captured
+    into a CUDA graph on a stream the library has never seen, and the replay
+    matches the oracle."""
+    lens = [3, 8192, 0, 70001, 5, 4097]
+    x, xt, s, c, offs = packed(lens, "f32", seed=9)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with forced_plan("batched", "f32", PATHS["bulk256"]):
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                api.sincos_batched(segs, lens_t)
+        torch.cuda.current_stream().wait_stream(side)
+        s.fill_(0)
+        c.fill_(0)
+        graph.replay()
+    torch.cuda.synchronize()
+    check_all(x, s, c, "f32", "plain", "normalized", "captured ring batch")
