@@ -397,7 +397,10 @@ class SinCosFn(torch.autograd.Function):
         return s, c
 
     @staticmethod
+    @torch.autograd.function.once_differentiable
     def backward(ctx, gs, gc):
+        # The kernel's gradient carries no graph of its own, so a second
+        # derivative is refused rather than silently taken as zero.
         s, c = ctx.saved_tensors
         gs = None if gs is None else gs.contiguous()
         gc = None if gc is None else gc.contiguous()

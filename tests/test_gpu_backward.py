@@ -90,3 +90,13 @@ def test_backward_in_place(cuda_lib):
     api.sincos_backward(gs_t, torch.from_numpy(gcn).cuda(), torch.from_numpy(so).cuda(),
                         torch.from_numpy(co).cuda(), gs_t)
     assert_f32_parity(as_np(gs_t), want, "in-place gx")
+
+
+def test_second_derivative_is_refused(cuda_lib):
+    """The hand-written backward is differentiable once: asking for a second
+    derivative raises instead of silently returning zero."""
+    x = torch.linspace(-3.0, 3.0, 1000, device="cuda").requires_grad_(True)
+    s, c = api.sincos_autograd(x)
+    (gx,) = torch.autograd.grad(s.sum() + 2.0 * c.sum(), x, create_graph=True)
+    with pytest.raises(RuntimeError):
+        torch.autograd.grad(gx.sum(), x)
