@@ -72,6 +72,43 @@ __device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint
                  :: "l"(dst), "r"(smem_addr(src_smem)), "r"(bytes) : "memory");
 }
 
+// Pairs of the E angles at element e of a staged input tile into the staged
+// output tiles (16-byte shared-memory accesses).
+template <int RED, int COEF, class OutT>
+__device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *co, int e)
+{
+    constexpr int E = Vec<OutT, 16>::E;
+    float in[E];
+#pragma unroll
+    for (int q = 0; q < E; q += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(xi + e + q);
+        in[q] = v.x;
+        in[q + 1] = v.y;
+        in[q + 2] = v.z;
+        in[q + 3] = v.w;
+    }
+    float sv[E], cv[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) pair<RED, COEF>(in[i], sv[i], cv[i]);
+    uint32_t ws[4], wc[4];
+    if constexpr (sizeof(OutT) == 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ws[i] = __float_as_uint(sv[i]);
+            wc[i] = __float_as_uint(cv[i]);
+        }
+    } else {
+        OutT *tag = nullptr;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ws[i] = pack2(tag, sv[2 * i], sv[2 * i + 1]);
+            wc[i] = pack2(tag, cv[2 * i], cv[2 * i + 1]);
+        }
+    }
+    *reinterpret_cast<uint4 *>(so + e) = make_uint4(ws[0], ws[1], ws[2], ws[3]);
+    *reinterpret_cast<uint4 *>(co + e) = make_uint4(wc[0], wc[1], wc[2], wc[3]);
+}
+
 template <class OutT, int RED, int COEF, int NT>
 __global__ void __launch_bounds__(NT)
 k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_t nchunks)
@@ -131,38 +168,8 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
         OutT *so = sout + b * kBulkChunk;
         OutT *co = cout + b * kBulkChunk;
 #pragma unroll
-        for (int j = 0; j < PER_THREAD; ++j) {
-            const int e = (j * NT + tid) * E;
-            float in[E];
-#pragma unroll
-            for (int q = 0; q < E; q += 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(xi + e + q);
-                in[q] = v.x;
-                in[q + 1] = v.y;
-                in[q + 2] = v.z;
-                in[q + 3] = v.w;
-            }
-            float sv[E], cv[E];
-#pragma unroll
-            for (int i = 0; i < E; ++i) pair<RED, COEF>(in[i], sv[i], cv[i]);
-            uint32_t ws[4], wc[4];
-            if constexpr (sizeof(OutT) == 4) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    ws[i] = __float_as_uint(sv[i]);
-                    wc[i] = __float_as_uint(cv[i]);
-                }
-            } else {
-                OutT *tag = nullptr;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    ws[i] = pack2(tag, sv[2 * i], sv[2 * i + 1]);
-                    wc[i] = pack2(tag, cv[2 * i], cv[2 * i + 1]);
-                }
-            }
-            *reinterpret_cast<uint4 *>(so + e) = make_uint4(ws[0], ws[1], ws[2], ws[3]);
-            *reinterpret_cast<uint4 *>(co + e) = make_uint4(wc[0], wc[1], wc[2], wc[3]);
-        }
+        for (int j = 0; j < PER_THREAD; ++j)
+            bulk_tile_vec<RED, COEF, OutT>(xi, so, co, (j * NT + tid) * E);
         // Make the tile visible to the bulk-copy (async) proxy, then let one
         // thread store it and refill this input stage.
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
