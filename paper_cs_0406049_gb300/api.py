@@ -201,7 +201,8 @@ def segments_from_lists(xs, ss, cs):
 
 def sincos_batched(segs: torch.Tensor, lens: torch.Tensor, out_dtype="f32",
                    reduction: str = "plain", coef: str = "normalized", stream=None) -> None:
-    """All segments in one prefix + persistent tile launch."""
+    """All segments at once: one self-scheduling launch with the binary32
+    default plan, a schedule kernel and a tile kernel with register plans."""
     count = lens.numel()
     with torch.cuda.device(lens.device):
         check(lib().sincos_batched_ex(_dev(segs, "segs"), _dev(lens, "lens", torch.int64), count,
