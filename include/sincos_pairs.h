@@ -227,8 +227,9 @@ int sincos_batched_release(void);
 int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *lens, int count,
                            int out_dtype, int reduction, int coef, sincos_stream_t stream);
 
-/* A batched launch captured once into a CUDA graph and replayed.  The graph
- * owns its scratch; the segs/lens device arrays are read at every replay,
+/* A batched launch captured once into a CUDA graph and replayed (launch
+ * infrastructure around the batched form of Sec. Methodology / Fig. 1; no
+ * paper counterpart).  The graph owns its scratch, if its plan needs one; the segs/lens device arrays are read at every replay,
  * so their contents (not their addresses) may change between replays. */
 typedef struct sincos_graph_s *sincos_graph;
 int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int count,
@@ -240,7 +241,8 @@ int sincos_batched_graph_destroy(sincos_graph g);
 /* Host buffers: chunked, pipelined host -> device -> host                   */
 /* ------------------------------------------------------------------------ */
 
-/* The forward on host arrays.  x_host (n floats) is copied to the device in
+/* The forward (Sec. Methodology, Fig. 1) on host arrays; the copy pipeline
+ * has no paper counterpart.  x_host (n floats) is copied to the device in
  * chunks, each chunk is computed, and s_host / c_host (n elements of
  * out_dtype) are copied back, with copies and kernels of different chunks
  * overlapped on internal streams.  Page-locked host memory gives full
@@ -269,17 +271,20 @@ typedef enum {
     SINCOS_OP_HUYGENS = 4   /* plan: block = threads per CTA, unroll = points per thread */
 } sincos_op;
 
-/* A launch configuration.
+/* A launch configuration.  The paper's only tuning knob is its 2-way
+ * software interleave (Sec. Results); these plans are the GPU analogue and
+ * have no other counterpart in it.
  * Register path (vec_bytes 16 or 32): threads per CTA, output vectors each
  * thread keeps in flight per iteration, resident CTAs per SM that the grid
  * is sized for, and the bytes of output one thread writes per vector and per
  * array (16: st.v4; 32: 256-bit st.v8).  A vector holds vec_bytes /
  * sizeof(out) pairs; a batched tile is block * unroll of them.
- * Bulk path (vec_bytes 0; forward and batched): TMA bulk copies stage
- * 8192-angle chunks (batched: tiles) through a two-stage shared-memory ring
- * and bulk stores write the results (up to 192 KB of shared memory, one CTA
- * per SM); block is 128, 256, 512 or 1024 and unroll / ctas_per_sm are not
- * used.  Single arrays shorter than one chunk, and the backward kernel, use
+ * Bulk path (vec_bytes 0; forward, exp(ix) and batched): TMA bulk copies
+ * stage 8192-angle chunks through a two-stage shared-memory ring and bulk
+ * stores write the results (192 KB of shared memory, one CTA per SM); block
+ * is 128, 256, 512 or 1024 and unroll / ctas_per_sm are not used.  The
+ * batched ring kernel runs min(block, 512) consumer threads plus one
+ * producer warp.  Single arrays shorter than one chunk, and the backward kernel, use
  * the 16-byte register path instead. */
 typedef struct {
     int block;        /* 64 .. 1024, multiple of 32 */
@@ -327,7 +332,7 @@ int sincos_plan_cache_save(const char *path);
 int sincos_plan_cache_load(const char *path);
 
 /* ------------------------------------------------------------------------ */
-/* Diagnostics                                                               */
+/* Diagnostics (no paper counterpart: the paper's routine returns no status)  */
 /* ------------------------------------------------------------------------ */
 
 const char *sincos_strerror(int status);
