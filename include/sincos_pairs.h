@@ -241,19 +241,26 @@ int sincos_batched_graph_destroy(sincos_graph g);
 /* Host buffers: chunked, pipelined host -> device -> host                   */
 /* ------------------------------------------------------------------------ */
 
-/* The forward (Sec. Methodology, Fig. 1) on host arrays; the copy pipeline
- * has no paper counterpart.  x_host (n floats) is copied to the device in
- * chunks, each chunk is computed, and s_host / c_host (n elements of
- * out_dtype) are copied back, with copies and kernels of different chunks
- * overlapped on internal streams.  Page-locked host memory gives full
- * overlap; pageable memory works but the copies are staged by the driver.
- *   dev_ws   caller-owned device workspace of ws_bytes, used as three
- *            rotating chunk buffers; sincos_host_workspace_bytes() gives the
- *            size for a given chunk length.  Must be 256-byte aligned.
+/* The forward (Sec. Methodology, Fig. 1) on host arrays; the data movement
+ * has no paper counterpart.  x_host holds n floats; s_host and c_host hold n
+ * elements of out_dtype.
+ *   If all three buffers are page-locked and mapped into the device's address
+ *   space (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping), one
+ *   kernel reads x and writes s and c across the host link itself
+ *   (zero-copy), and dev_ws is not used.  x may be s or c exactly (binary32
+ *   output); any other overlap returns SINCOS_EOVERLAP.
+ *   Otherwise x is copied to the device in chunks, each chunk is computed,
+ *   and s and c are copied back, with copies and kernels of different chunks
+ *   overlapped on internal streams (pageable memory works, but the driver
+ *   stages its copies).
+ *   dev_ws   caller-owned device workspace of ws_bytes for the chunked path,
+ *            used as three rotating chunk buffers; sincos_host_workspace_bytes()
+ *            gives the size for a given chunk length.  Must be 256-byte
+ *            aligned, and is required on both paths.
  * The call is ordered after earlier work on `stream`, and later work on
- * `stream` waits for all its copies.  Host buffers must stay valid until
- * then.  The library creates its internal streams and events once per
- * device, on first use. */
+ * `stream` waits for all its reads and writes of the host buffers, which must
+ * stay valid until then.  The library creates its internal streams and events
+ * once per device, on first use of the chunked path. */
 int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n,
                       int out_dtype, int reduction, int coef, void *dev_ws, size_t ws_bytes,
                       sincos_stream_t stream);

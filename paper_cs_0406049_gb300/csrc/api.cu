@@ -24,13 +24,6 @@ bool g_dev_ready[kMaxDevices] = {false};
 std::mutex g_occ_mu;
 std::unordered_map<uint64_t, int> g_occ;   // (kernel, block, device) -> resident CTAs per SM
 
-bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes)
-{
-    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + abytes;
-    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + bbytes;
-    return a0 < b1 && b0 < a1;
-}
-
 }  // namespace
 
 int cuda_fail(cudaError_t e, const char *what)

@@ -47,6 +47,14 @@ sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n);
 bool plan_valid(const sincos_plan &p);
 // The plan's forward path: 0 = bulk (TMA-staged) kernel, 16 or 32 = register
 // path with that many bytes per thread per output vector.
+// Whether byte ranges [a, a + abytes) and [b, b + bbytes) share a byte.
+inline bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes)
+{
+    const uintptr_t a0 = (uintptr_t)a, a1 = a0 + abytes;
+    const uintptr_t b0 = (uintptr_t)b, b1 = b0 + bbytes;
+    return a0 < b1 && b0 < a1;
+}
+
 inline int plan_vec_bytes(const sincos_plan &p) { return p.vec_bytes == 0 ? 0 : p.vec_bytes == 16 ? 16 : 32; }
 // The register-path width for kernels without a bulk variant.
 inline int reg_vec_bytes(const sincos_plan &p) { return p.vec_bytes == 32 ? 32 : 16; }

@@ -37,6 +37,45 @@ def test_host_path_chunks(cuda_lib, dtype, pinned):
         assert_16_parity(as_np(ch), want_c, dtype == "bf16", "host c")
 
 
+def test_host_path_mixed_memory_kinds(cuda_lib):
+    """Page-locked x with pageable outputs goes through the chunked copies;
+    the results are the same."""
+    n = (1 << 19) + 77
+    x = mixed_angles(n, seed=10)
+    xh = torch.from_numpy(x).pin_memory()
+    sh = torch.empty(n)
+    ch = torch.empty(n).pin_memory()
+    ws = torch.empty(api.sincos_host_workspace_bytes("f32", 65536), dtype=torch.uint8,
+                     device="cuda")
+    api.sincos_pairs_host(xh, sh, ch, ws)
+    torch.cuda.synchronize()
+    want_s, want_c = oracle.sincos(x)
+    assert_f32_parity(sh.numpy(), want_s, "mixed s")
+    assert_f32_parity(ch.numpy(), want_c, "mixed c")
+
+
+def test_host_path_zero_copy_in_place_and_overlap(cuda_lib):
+    """Page-locked buffers: s may be x itself (binary32), a partial overlap is
+    refused before anything runs."""
+    n = (1 << 18) + 3
+    x = mixed_angles(n, seed=11)
+    buf = torch.from_numpy(x).pin_memory()
+    ch = torch.empty(n).pin_memory()
+    ws = torch.empty(api.sincos_host_workspace_bytes("f32", 4096), dtype=torch.uint8,
+                     device="cuda")
+    api.sincos_pairs_host(buf, buf, ch, ws)
+    torch.cuda.synchronize()
+    want_s, want_c = oracle.sincos(x)
+    assert_f32_parity(buf.numpy(), want_s, "in-place s")
+    assert_f32_parity(ch.numpy(), want_c, "in-place c")
+    big = torch.from_numpy(mixed_angles(n + 1, seed=12)).pin_memory()
+    before = big.clone()
+    with pytest.raises(RuntimeError):
+        api.sincos_pairs_host(big[:n], big[1:], ch, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(big.view(torch.int32), before.view(torch.int32))   # bits: NaNs included
+
+
 def test_autotune_pairs_and_plan_cache(cuda_lib, tmp_path):
     n = 1 << 22
     x = mixed_angles(n, seed=10)
