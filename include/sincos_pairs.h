@@ -29,8 +29,9 @@
  *              legacy default stream).  SINCOS_OK means "enqueued"; results
  *              are valid once the stream has reached that point.
  *   Errors     Invalid arguments are rejected on the host before anything is
- *              enqueued: SINCOS_EINVAL (null pointer with n > 0, n < 0, bad
- *              enum), SINCOS_EOVERLAP (outputs overlap each other, or the
+ *              enqueued: SINCOS_EINVAL (null pointer with n > 0, a pointer
+ *              not aligned to its element type, n < 0, bad enum),
+ *              SINCOS_EOVERLAP (outputs overlap each other, or the
  *              input partially overlaps an output).  A failed CUDA call gives
  *              SINCOS_ECUDA and its text is kept for sincos_last_error().
  *              n == 0 (or count == 0) returns SINCOS_OK and enqueues nothing.
@@ -167,7 +168,11 @@ int sincos_backward(const float *gs, const float *gc, const float *s, const floa
 /* ------------------------------------------------------------------------ */
 
 /* One array of the batch: x has lens[i] floats; s and c have lens[i]
- * elements of the batch's output dtype.  All three are device pointers. */
+ * elements of the batch's output dtype.  All three are device pointers,
+ * each aligned to its element type (4 bytes for x and binary32 outputs, 2
+ * for 16-bit outputs).  The descriptors live on the device, so the library
+ * cannot check them: a misaligned or invalid pointer in a descriptor is
+ * undefined behaviour (the kernels may fault). */
 typedef struct {
     const float *x;
     void *s;

@@ -162,6 +162,7 @@ int sincos_pairs_ex(const float *x, void *s, void *c, int64_t n, int out_dtype, 
     if (n == 0) return SINCOS_OK;
     if (!x || !s || !c) return SINCOS_EINVAL;
     const size_t osz = (size_t)dtype_size(out_dtype);
+    if (!aligned_to(x, 4) || !aligned_to(s, osz) || !aligned_to(c, osz)) return SINCOS_EINVAL;
     const size_t xb = (size_t)n * 4, ob = (size_t)n * osz;
     if (ranges_overlap(s, ob, c, ob)) return SINCOS_EOVERLAP;
     bool in_place = false;
@@ -190,6 +191,7 @@ int sincos_backward(const float *gs, const float *gc, const float *s, const floa
     if (n < 0) return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
     if (!gx || ((gs || gc) && (!s || !c))) return SINCOS_EINVAL;
+    if (!all_float_aligned({gs, gc, s, c, gx})) return SINCOS_EINVAL;
     const size_t b = (size_t)n * 4;
     bool in_place = false;
     for (const float *in : {gs, gc, gs ? c : nullptr, gc ? s : nullptr}) {

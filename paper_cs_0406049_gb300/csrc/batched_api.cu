@@ -34,6 +34,7 @@ int validate(const sincos_seg *segs, const int64_t *lens, int count, int dtype, 
     if (count < 0 || !valid_dtype(dtype) || !valid_reduction(red) || !valid_coef(coef))
         return SINCOS_EINVAL;
     if (count > 0 && (!segs || !lens)) return SINCOS_EINVAL;
+    if (count > 0 && (!aligned_to(segs, 8) || !aligned_to(lens, 8))) return SINCOS_EINVAL;
     return SINCOS_OK;
 }
 

@@ -65,6 +65,7 @@ extern "C" int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *len
         return SINCOS_EINVAL;
     if (count == 0) return SINCOS_OK;
     if (!segs || !lens) return SINCOS_EINVAL;
+    if (!aligned_to(segs, 8) || !aligned_to(lens, 8)) return SINCOS_EINVAL;
     if (count > SINCOS_NOALLOC_MAX_SEGMENTS) return SINCOS_EUNSUPPORTED;
     const DeviceInfo *dev = nullptr;
     int rc = current_device(&dev);

@@ -293,6 +293,7 @@ extern "C" int sincos_expi(const float *x, float *z, int64_t n, int reduction, i
     if (n < 0 || !valid_reduction(reduction) || !valid_coef(coef)) return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
     if (!x || !z) return SINCOS_EINVAL;
+    if (!all_float_aligned({x, z})) return SINCOS_EINVAL;
     const uintptr_t x0 = (uintptr_t)x, z0 = (uintptr_t)z;
     if (x0 < z0 + 8u * (uint64_t)n && z0 < x0 + 4u * (uint64_t)n) return SINCOS_EOVERLAP;
     const DeviceInfo *dev = nullptr;

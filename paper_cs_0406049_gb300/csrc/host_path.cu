@@ -99,6 +99,9 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
         return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
     if (!x_host || !s_host || !c_host || !dev_ws || ((uintptr_t)dev_ws & 255u)) return SINCOS_EINVAL;
+    if (!aligned_to(x_host, 4) || !aligned_to(s_host, (size_t)dtype_size(out_dtype)) ||
+        !aligned_to(c_host, (size_t)dtype_size(out_dtype)))
+        return SINCOS_EINVAL;
     const int64_t slot = slot_elems_for(out_dtype, ws_bytes);
     if (slot < 64) return SINCOS_EINVAL;
     const size_t osz = (size_t)dtype_size(out_dtype);

@@ -143,6 +143,7 @@ int huygens_check(const float *px, const float *py, const float *pz, int64_t m,
     if (m == 0) return SINCOS_OK;
     if (!px || !py || !pz || !u) return SINCOS_EINVAL;
     if (n > 0 && (!qx || !qy || !qz || !ar || !ai)) return SINCOS_EINVAL;
+    if (!all_float_aligned({px, py, pz, qx, qy, qz, ar, ai, u})) return SINCOS_EINVAL;
     for (const float *p : {px, py, pz})
         if (overlaps_output(p, m, u, m)) return SINCOS_EOVERLAP;
     if (n > 0)

@@ -2,6 +2,8 @@
 // units.  Not part of the public ABI (that is include/sincos_pairs.h).
 #pragma once
 
+#include <initializer_list>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,6 +49,21 @@ sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n);
 bool plan_valid(const sincos_plan &p);
 // The plan's forward path: 0 = bulk (TMA-staged) kernel, 16 or 32 = register
 // path with that many bytes per thread per output vector.
+// Whether p is a multiple of `bytes` (a power of two): element alignment of
+// the arrays the entry points take (floats 4, 16-bit outputs 2).
+inline bool aligned_to(const void *p, size_t bytes)
+{
+    return ((uintptr_t)p & (bytes - 1)) == 0;
+}
+
+// Every non-null pointer of the list aligned to 4 bytes.
+inline bool all_float_aligned(std::initializer_list<const void *> ps)
+{
+    for (const void *p : ps)
+        if (p && !aligned_to(p, 4)) return false;
+    return true;
+}
+
 // Whether byte ranges [a, a + abytes) and [b, b + bbytes) share a byte.
 inline bool ranges_overlap(const void *a, size_t abytes, const void *b, size_t bbytes)
 {

@@ -296,6 +296,9 @@ int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_d
     if (n <= 0 || !x || !s || !c || !valid_dtype(out_dtype) || !valid_reduction(reduction) ||
         !valid_coef(coef))
         return SINCOS_EINVAL;
+    if (!aligned_to(x, 4) || !aligned_to(s, dtype_size(out_dtype)) ||
+        !aligned_to(c, dtype_size(out_dtype)))
+        return SINCOS_EINVAL;
     const size_t xb = (size_t)n * 4, ob = (size_t)n * dtype_size(out_dtype);
     const uintptr_t x0 = (uintptr_t)x;
     for (const void *o : {(const void *)s, (const void *)c})
@@ -318,6 +321,7 @@ int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int
     SINCOS_TRACE("sincos_autotune_expi");
     if (n <= 0 || !x || !z || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
+    if (!all_float_aligned({x, z})) return SINCOS_EINVAL;
     const uintptr_t x0 = (uintptr_t)x, z0 = (uintptr_t)z;
     if (x0 < z0 + 8u * (uint64_t)n && z0 < x0 + 4u * (uint64_t)n) return SINCOS_EOVERLAP;
     const DeviceInfo *dev = nullptr;
@@ -341,6 +345,7 @@ int sincos_autotune_huygens(const float *px, const float *py, const float *pz, i
     if (m <= 0 || n < 0 || !px || !py || !pz || !u || !valid_reduction(reduction))
         return SINCOS_EINVAL;
     if (n > 0 && (!qx || !qy || !qz || !ar || !ai)) return SINCOS_EINVAL;
+    if (!all_float_aligned({px, py, pz, qx, qy, qz, ar, ai, u})) return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
@@ -359,6 +364,7 @@ int sincos_autotune_backward(const float *gs, const float *gc, const float *s, c
 {
     SINCOS_TRACE("sincos_autotune_backward");
     if (n <= 0 || !gx || !s || !c) return SINCOS_EINVAL;
+    if (!all_float_aligned({gs, gc, s, c, gx})) return SINCOS_EINVAL;
     for (const float *in : {gs, gc, s, c})
         if (in && (uintptr_t)in < (uintptr_t)(gx + n) && (uintptr_t)gx < (uintptr_t)(in + n))
             return SINCOS_EOVERLAP;
@@ -382,6 +388,7 @@ int sincos_autotune_batched(const sincos_seg *segs, const int64_t *lens, int cou
     if (count <= 0 || !segs || !lens || !valid_dtype(out_dtype) || !valid_reduction(reduction) ||
         !valid_coef(coef))
         return SINCOS_EINVAL;
+    if (!aligned_to(segs, 8) || !aligned_to(lens, 8)) return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;

@@ -149,3 +149,26 @@ def test_huygens_validation(lib):
     assert f(*P, 8, None, *Q[1:], 8, 6.28, 1, U, None) == _lib.EINVAL
     assert f(*P, 8, *Q, 8, 6.28, 1, A + 4, None) == _lib.EOVERLAP      # u over px
     assert f(*P, 0, *Q, 8, 6.28, 1, U, None) == _lib.OK
+
+
+def test_misaligned_pointers_are_rejected(lib):
+    """A pointer not aligned to its element type is an invalid argument: the
+    kernels' vector paths assume element alignment, so such a call must not
+    reach the device."""
+    stream = None
+    assert lib.sincos_pairs_ex(A + 2, A + 4096, A + 8192, 8, 0, 0, 0, stream) == _lib.EINVAL
+    assert lib.sincos_pairs_ex(A, A + 4097, A + 8192, 8, 0, 0, 0, stream) == _lib.EINVAL
+    assert lib.sincos_pairs_ex(A, A + 4096, A + 8193, 8, 1, 0, 0, stream) == _lib.EINVAL  # bf16
+    assert lib.sincos_pairs(A + 1, A + 4096, A + 8192, 8, stream) == _lib.EINVAL
+    assert lib.sincos_backward(A + 1, None, A + 8192, A + 12288, A + 16384, 8, stream) == _lib.EINVAL
+    assert lib.sincos_backward(A, A + 4096, A + 8192, A + 12288, A + 16386, 8, stream) == _lib.EINVAL
+    assert lib.sincos_expi(A, A + 4098, 8, 0, 0, stream) == _lib.EINVAL
+    assert lib.sincos_batched(A + 4, A + 4096, 4, stream) == _lib.EINVAL       # descriptors: 8 B
+    assert lib.sincos_batched(A, A + 4100, 4, stream) == _lib.EINVAL          # lengths: 8 B
+    assert lib.sincos_batched_noalloc(A + 4, A + 4096, 4, 0, 0, 0, stream) == _lib.EINVAL
+    ws = A
+    assert lib.sincos_pairs_host(A + 2, A + 4096, A + 8192, 8, 0, 0, 0, ws, 1 << 20, stream) == \
+        _lib.EINVAL
+    best = _lib.sincos_plan()
+    assert lib.sincos_autotune_pairs(A + 2, A + 4096, A + 8192, 8, 0, 0, 0, stream,
+                                     ctypes.byref(best)) == _lib.EINVAL
