@@ -33,10 +33,9 @@ namespace sincos_gb300 {
 // with the stage's byte count) and empty[st] (every consumer arrives once it
 // has read the stage's input); descriptor slots that outlive their stage by
 // one round (see kRingSlots); a named barrier among the consumers; bulk-store
-// groups for the two output stages.  Every
-// wait is bounded.  A wait that gives up counts a timeout and stops its side;
-// the producer then waits (bounded) for every copy it issued before the CTA
-// may exit.
+// groups for the two output stages.  Every wait is bounded.  A wait that
+// gives up counts a timeout and stops its side; the producer then waits
+// (bounded) for every copy it issued before the CTA may exit.
 // ---------------------------------------------------------------------------
 
 constexpr int kRingStages = 2;
@@ -279,7 +278,7 @@ __device__ __forceinline__ int64_t ring_tile_lo(int64_t k, int h)
 // parts that fill each stage to kRingCap angles (a range that does not fit is
 // split on a 32-angle boundary of its grid), so every stage but the last
 // carries a full load however the segments are sized.
-template <class OutT, int NT>
+template <class OutT>
 __device__ __forceinline__ void ring_producer(const sincos_seg *segs, const int64_t *lens,
                                               int count, const RingRun run, float *xin,
                                               RingPart (*parts)[kRingMaxParts], int *nparts,
@@ -447,8 +446,8 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
     __syncthreads();
 
     if (tid >= NT) {
-        ring_producer<OutT, NT>(segs, lens, count, run, xin, parts, nparts, nedges, nmid, nout,
-                                full, empty, &give_up);
+        ring_producer<OutT>(segs, lens, count, run, xin, parts, nparts, nedges, nmid, nout,
+                            full, empty, &give_up);
         return;
     }
 
