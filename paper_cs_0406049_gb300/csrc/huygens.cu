@@ -128,11 +128,10 @@ using namespace sincos_gb300;
 
 namespace {
 
+// Whether cnt floats at `in` share a byte with the m complex64 outputs at u.
 bool overlaps_output(const float *in, int64_t cnt, const float *u, int64_t m)
 {
-    const uintptr_t a0 = (uintptr_t)in, a1 = a0 + 4u * (uint64_t)cnt;
-    const uintptr_t b0 = (uintptr_t)u, b1 = b0 + 8u * (uint64_t)m;
-    return a0 < b1 && b0 < a1;
+    return ranges_overlap(in, 4u * (size_t)cnt, u, 8u * (size_t)m);
 }
 
 int huygens_check(const float *px, const float *py, const float *pz, int64_t m,
