@@ -105,11 +105,7 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
     const int64_t slot = slot_elems_for(out_dtype, ws_bytes);
     if (slot < 64) return SINCOS_EINVAL;
     const size_t osz = (size_t)dtype_size(out_dtype);
-    {
-        const uintptr_t s0 = (uintptr_t)s_host, c0 = (uintptr_t)c_host;
-        const size_t ob = (size_t)n * osz;
-        if (s0 < c0 + ob && c0 < s0 + ob) return SINCOS_EOVERLAP;
-    }
+    if (ranges_overlap(s_host, (size_t)n * osz, c_host, (size_t)n * osz)) return SINCOS_EOVERLAP;
     const DeviceInfo *dev = nullptr;
     int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;

@@ -300,9 +300,8 @@ int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_d
         !aligned_to(c, dtype_size(out_dtype)))
         return SINCOS_EINVAL;
     const size_t xb = (size_t)n * 4, ob = (size_t)n * dtype_size(out_dtype);
-    const uintptr_t x0 = (uintptr_t)x;
     for (const void *o : {(const void *)s, (const void *)c})
-        if (x0 < (uintptr_t)o + ob && (uintptr_t)o < x0 + xb) return SINCOS_EOVERLAP;
+        if (ranges_overlap(x, xb, o, ob)) return SINCOS_EOVERLAP;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
@@ -322,8 +321,7 @@ int sincos_autotune_expi(const float *x, float *z, int64_t n, int reduction, int
     if (n <= 0 || !x || !z || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
     if (!all_float_aligned({x, z})) return SINCOS_EINVAL;
-    const uintptr_t x0 = (uintptr_t)x, z0 = (uintptr_t)z;
-    if (x0 < z0 + 8u * (uint64_t)n && z0 < x0 + 4u * (uint64_t)n) return SINCOS_EOVERLAP;
+    if (ranges_overlap(x, 4u * (size_t)n, z, 8u * (size_t)n)) return SINCOS_EOVERLAP;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
@@ -366,8 +364,7 @@ int sincos_autotune_backward(const float *gs, const float *gc, const float *s, c
     if (n <= 0 || !gx || !s || !c) return SINCOS_EINVAL;
     if (!all_float_aligned({gs, gc, s, c, gx})) return SINCOS_EINVAL;
     for (const float *in : {gs, gc, s, c})
-        if (in && (uintptr_t)in < (uintptr_t)(gx + n) && (uintptr_t)gx < (uintptr_t)(in + n))
-            return SINCOS_EOVERLAP;
+        if (in && ranges_overlap(in, 4u * (size_t)n, gx, 4u * (size_t)n)) return SINCOS_EOVERLAP;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
