@@ -657,7 +657,8 @@ def run_ours(args, dist: Dist):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth",
-                         "kernel": (f"k_forward_bulk<float, plain, normalized, {plan['block']}>"
+                         "kernel": (f"k_forward_bulk<float, plain, normalized, {plan['block']}, "
+                                    f"{4096 if plan['ctas_per_sm'] >= 2 else 8192}>"
                                     if plan["vec_bytes"] == 0 else
                                     f"k_forward<float, plain, normalized, {plan['unroll']}, "
                                     f"{plan['vec_bytes']}>"),

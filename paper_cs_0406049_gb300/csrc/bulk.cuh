@@ -31,10 +31,14 @@ constexpr unsigned kBulkSpinLimit = 1u << 20;
 // Per translation unit; each TU that launches bulk kernels reports its own.
 static __device__ unsigned int g_bulk_wait_timeouts = 0;
 
-template <class OutT>
+// Chunk of the small-stage variant: 4096 angles, so that two (binary32
+// outputs) or three (16-bit outputs) CTAs fit in an SM's shared memory.
+constexpr int kBulkSmallChunk = 4096;
+
+template <class OutT, int CH = kBulkChunk>
 constexpr size_t bulk_smem_bytes()
 {
-    return (size_t)kBulkStages * kBulkChunk * 4 + 4 * (size_t)kBulkChunk * sizeof(OutT);
+    return (size_t)kBulkStages * CH * 4 + 4 * (size_t)CH * sizeof(OutT);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -109,17 +113,17 @@ __device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *c
     *reinterpret_cast<uint4 *>(co + e) = make_uint4(wc[0], wc[1], wc[2], wc[3]);
 }
 
-template <class OutT, int RED, int COEF, int NT>
+template <class OutT, int RED, int COEF, int NT, int CH>
 __global__ void __launch_bounds__(NT)
 k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_t nchunks)
 {
     constexpr int E = Vec<OutT, 16>::E;                       // pairs per 16-byte output vector
-    constexpr int PER_THREAD = kBulkChunk / (NT * E);         // output vectors per thread per chunk
-    static_assert(kBulkChunk % (NT * E) == 0, "chunk must split evenly over the CTA");
+    constexpr int PER_THREAD = CH / (NT * E);         // output vectors per thread per chunk
+    static_assert(CH % (NT * E) == 0, "chunk must split evenly over the CTA");
     extern __shared__ __align__(128) unsigned char smem[];
     float *xin = (float *)smem;                                        // [stages][chunk]
-    OutT *sout = (OutT *)(xin + kBulkStages * kBulkChunk);              // [2][chunk]
-    OutT *cout = sout + 2 * kBulkChunk;                                 // [2][chunk]
+    OutT *sout = (OutT *)(xin + kBulkStages * CH);              // [2][chunk]
+    OutT *cout = sout + 2 * CH;                                 // [2][chunk]
     __shared__ __align__(8) uint64_t full[kBulkStages];
     __shared__ int64_t issued[kBulkStages];
     __shared__ int give_up;
@@ -142,7 +146,7 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
         for (int st = 0; st < kBulkStages; ++st) {
             const int64_t ch = blockIdx.x + (int64_t)st * gridDim.x;
             if (ch < nchunks) {
-                bulk_load(xin + st * kBulkChunk, xg + ch * kBulkChunk, kBulkChunk * 4,
+                bulk_load(xin + st * CH, xg + ch * CH, CH * 4,
                           smem_addr(&full[st]));
                 issued[st] += 1;
             }
@@ -164,9 +168,9 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
         if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncthreads();
         if (give_up) break;
-        const float *xi = xin + st * kBulkChunk;
-        OutT *so = sout + b * kBulkChunk;
-        OutT *co = cout + b * kBulkChunk;
+        const float *xi = xin + st * CH;
+        OutT *so = sout + b * CH;
+        OutT *co = cout + b * CH;
 #pragma unroll
         for (int j = 0; j < PER_THREAD; ++j)
             bulk_tile_vec<RED, COEF, OutT>(xi, so, co, (j * NT + tid) * E);
@@ -175,12 +179,12 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
-            bulk_store(sg + ch * kBulkChunk, so, kBulkChunk * sizeof(OutT));
-            bulk_store(cg + ch * kBulkChunk, co, kBulkChunk * sizeof(OutT));
+            bulk_store(sg + ch * CH, so, CH * sizeof(OutT));
+            bulk_store(cg + ch * CH, co, CH * sizeof(OutT));
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             const int64_t next = blockIdx.x + (k + kBulkStages) * gridDim.x;
             if (next < nchunks) {
-                bulk_load(xin + st * kBulkChunk, xg + next * kBulkChunk, kBulkChunk * 4,
+                bulk_load(xin + st * CH, xg + next * CH, CH * 4,
                           smem_addr(&full[st]));
                 issued[st] += 1;
             }
@@ -199,7 +203,7 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
 
     // Angles after the last whole chunk: 16-byte vectors spread over the CTAs,
     // then single elements; the head before the aligned start goes to CTA 0.
-    const int64_t rest0 = nchunks * kBulkChunk;                // relative to head
+    const int64_t rest0 = nchunks * CH;                // relative to head
     const int64_t nrest = (n - head - rest0) / E;
     for (int64_t v = blockIdx.x * (int64_t)NT + tid; v < nrest; v += (int64_t)gridDim.x * NT) {
         float in[E];
@@ -217,19 +221,19 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
 // CTAs per SM at that size.
 int bulk_resident_ctas(const void *kernel, int block, size_t smem);
 
-template <class OutT, int RED, int COEF, int NT>
+template <class OutT, int RED, int COEF, int NT, int CH = kBulkChunk>
 static int launch_forward_bulk_nt(const float *x, OutT *s, OutT *c, int64_t n, int64_t head,
                                   const DeviceInfo &dev, cudaStream_t st)
 {
-    const void *fn = (const void *)k_forward_bulk<OutT, RED, COEF, NT>;
-    constexpr size_t smem = bulk_smem_bytes<OutT>();
+    const void *fn = (const void *)k_forward_bulk<OutT, RED, COEF, NT, CH>;
+    constexpr size_t smem = bulk_smem_bytes<OutT, CH>();
     const int per_sm = bulk_resident_ctas(fn, NT, smem);
     if (per_sm <= 0) return SINCOS_EUNSUPPORTED;
-    const int64_t nchunks = (n - head) / kBulkChunk;
+    const int64_t nchunks = (n - head) / CH;
     int64_t grid = (int64_t)per_sm * dev.sms;
     if (nchunks < grid) grid = nchunks > 0 ? nchunks : 1;
-    k_forward_bulk<OutT, RED, COEF, NT><<<(unsigned)grid, NT, smem, st>>>(x, s, c, n, head,
-                                                                          nchunks);
+    k_forward_bulk<OutT, RED, COEF, NT, CH><<<(unsigned)grid, NT, smem, st>>>(x, s, c, n, head,
+                                                                              nchunks);
     return check_launch("bulk forward kernel launch");
 }
 

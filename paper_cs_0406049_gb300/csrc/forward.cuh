@@ -111,8 +111,24 @@ static int launch_forward_rc(const float *x, OutT *s, OutT *c, int64_t n, bool i
                              const sincos_plan &plan, const DeviceInfo &dev, cudaStream_t st)
 {
     // Bulk (TMA-staged) path when the plan asks for it and the array holds at
-    // least one whole chunk after its aligned start.
-    if (plan_vec_bytes(plan) == 0) {
+    // least one whole chunk after its aligned start.  ctas_per_sm >= 2 asks
+    // for the small-stage variant (several CTAs per SM).
+    if (plan_vec_bytes(plan) == 0 && plan.ctas_per_sm >= 2) {
+        const int h = vector_head<OutT, 16>(x, s, c);
+        if (h >= 0 && n - h >= kBulkSmallChunk) {
+            switch (plan.block) {
+            case 128:
+                return launch_forward_bulk_nt<OutT, RED, COEF, 128, kBulkSmallChunk>(x, s, c, n, h,
+                                                                                      dev, st);
+            case 256:
+                return launch_forward_bulk_nt<OutT, RED, COEF, 256, kBulkSmallChunk>(x, s, c, n, h,
+                                                                                      dev, st);
+            default:
+                return launch_forward_bulk_nt<OutT, RED, COEF, 512, kBulkSmallChunk>(x, s, c, n, h,
+                                                                                      dev, st);
+            }
+        }
+    } else if (plan_vec_bytes(plan) == 0) {
         const int h = vector_head<OutT, 16>(x, s, c);
         if (h >= 0 && n - h >= kBulkChunk) {
             switch (plan.block) {

@@ -164,6 +164,8 @@ std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
     }
     if (op != SINCOS_OP_BACKWARD)   // bulk path: one CTA per SM, CTA size only
         for (int block : {128, 256, 512, 1024}) out.push_back(sincos_plan{block, 2, 1, 0});
+    if (op == SINCOS_OP_PAIRS)      // bulk path with 4096-angle stages, several CTAs per SM
+        for (int block : {128, 256, 512}) out.push_back(sincos_plan{block, 2, 2, 0});
     const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
     for (int vec : {16, 32})
         for (int block : {128, 256, 512, 1024})

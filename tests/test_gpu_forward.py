@@ -84,7 +84,8 @@ OFFSETS = {
 }
 
 
-PATHS = {"bulk": (512, 2, 1, 0), "reg16": (256, 8, 4, 16), "reg32": (256, 4, 4, 32)}
+PATHS = {"bulk": (512, 2, 1, 0), "bulk_small": (256, 2, 2, 0), "reg16": (256, 8, 4, 16),
+         "reg32": (256, 4, 4, 32)}
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
@@ -119,6 +120,26 @@ def test_bulk_path_chunk_boundaries(cuda_lib, dtype, block):
             for offs in OFFSETS[dtype][:2]:
                 s, c = run_guarded(x, dtype, "plain", "normalized", offs)
                 check(dtype, s, c, want_s, want_c, f"bulk{block} {dtype} n={n} offs={offs}")
+    assert api.sincos_device_wait_timeouts() == 0
+
+
+SMALL_BULK_SIZES = [4095, 4096, 4097, 4096 + 31, 2 * 4096 + 5, 456 * 4096, 456 * 4096 + 4095,
+                    457 * 4096 - 1, 2000 * 4096 + 2049]
+
+
+@pytest.mark.parametrize("block", [128, 256, 512])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_small_stage_bulk_path_chunk_boundaries(cuda_lib, dtype, block):
+    """The 4096-angle-stage variant (several CTAs per SM): whole chunks, tails
+    and heads around its chunk and its larger grid."""
+    with forced_plan("pairs", dtype, (block, 2, 2, 0)):
+        for n in SMALL_BULK_SIZES:
+            x = mixed_angles(n, seed=n + block + 1)
+            want_s, want_c = oracle_out(x, dtype, "compensated", "normalized")
+            for offs in OFFSETS[dtype][:2]:
+                s, c = run_guarded(x, dtype, "compensated", "normalized", offs)
+                check(dtype, s, c, want_s, want_c,
+                      f"small bulk{block} {dtype} n={n} offs={offs}")
     assert api.sincos_device_wait_timeouts() == 0
 
 
