@@ -13,6 +13,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "trace.h"
@@ -176,38 +177,38 @@ std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
     return out;
 }
 
-// Median of `reps` timed runs of `launch` on `st` (after one warm-up run), in
-// milliseconds; a negative value if any launch fails.
-template <class F>
-float time_plan(F &&launch, cudaStream_t st, int reps)
-{
-    cudaEvent_t a, b;
-    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
-    if (cudaEventCreate(&b) != cudaSuccess) {
-        cudaEventDestroy(a);
-        return -1.f;
+// Event-timed launches on one stream.
+struct LaunchTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool ok = false;
+    LaunchTimer()
+    {
+        ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
     }
-    std::vector<float> ms;
-    bool ok = launch() == SINCOS_OK;
-    for (int r = 0; ok && r < reps; ++r) {
+    ~LaunchTimer()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    // Duration of one run of `launch` on `st` in milliseconds, or -1.
+    template <class F>
+    float once(F &&launch, cudaStream_t st)
+    {
+        if (!ok) return -1.f;
         cudaEventRecord(a, st);
-        ok = launch() == SINCOS_OK;
+        if (launch() != SINCOS_OK) return -1.f;
         cudaEventRecord(b, st);
-        if (ok && cudaEventSynchronize(b) == cudaSuccess) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, a, b);
-            ms.push_back(t);
-        } else {
-            ok = false;
-        }
+        float t = 0.f;
+        if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess)
+            return -1.f;
+        return t;
     }
-    cudaStreamSynchronize(st);
-    cudaGetLastError();
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    if (!ok || ms.empty()) return -1.f;
-    std::sort(ms.begin(), ms.end());
-    return ms[ms.size() / 2];
+};
+
+float median_of(std::vector<float> v)
+{
+    std::sort(v.begin(), v.end());
+    return v[v.size() / 2];
 }
 
 bool stream_is_capturing(cudaStream_t st)
@@ -220,18 +221,57 @@ bool stream_is_capturing(cudaStream_t st)
     return cs != cudaStreamCaptureStatusNone;
 }
 
+// Two rounds.  The screen times every candidate (one warm-up run, median of
+// three); with a hundred candidates the single fastest median is often a
+// lucky one, so the few fastest are then timed again round-robin -- one run
+// of each per pass, so that a change of clock or of L2 state shifts them all
+// alike -- and the lowest median of those passes wins.
+constexpr int kScreenReps = 3;
+constexpr int kFinalists = 6;
+constexpr int kConfirmPasses = 9;
+
 template <class F>
 int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F &&launch_with,
          sincos_plan *best)
 {
     if (stream_is_capturing(st)) return SINCOS_ECAPTURE;
-    float best_ms = -1.f;
-    sincos_plan best_plan = default_plan(op, dtype);
+    LaunchTimer timer;
+    if (!timer.ok) return SINCOS_ECUDA;
+    std::vector<std::pair<float, sincos_plan>> screened;
     for (const sincos_plan &p : candidates(dev, op)) {
-        const float ms = time_plan([&] { return launch_with(p); }, st, 3);
-        if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
-            best_ms = ms;
-            best_plan = p;
+        auto run = [&] { return launch_with(p); };
+        if (run() != SINCOS_OK) continue;
+        std::vector<float> ms;
+        for (int r = 0; r < kScreenReps; ++r) {
+            const float t = timer.once(run, st);
+            if (t < 0.f) break;
+            ms.push_back(t);
+        }
+        if ((int)ms.size() == kScreenReps) screened.emplace_back(median_of(ms), p);
+    }
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    if (screened.empty()) return SINCOS_ECUDA;
+    std::stable_sort(screened.begin(), screened.end(),
+                     [](const auto &l, const auto &r) { return l.first < r.first; });
+    if ((int)screened.size() > kFinalists) screened.resize(kFinalists);
+
+    std::vector<std::vector<float>> ms(screened.size());
+    for (int pass = 0; pass < kConfirmPasses; ++pass)
+        for (size_t i = 0; i < screened.size(); ++i) {
+            const float t = timer.once([&] { return launch_with(screened[i].second); }, st);
+            if (t > 0.f) ms[i].push_back(t);
+        }
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    float best_ms = -1.f;
+    sincos_plan best_plan = screened[0].second;
+    for (size_t i = 0; i < screened.size(); ++i) {
+        if (ms[i].empty()) continue;
+        const float t = median_of(ms[i]);
+        if (best_ms < 0.f || t < best_ms) {
+            best_ms = t;
+            best_plan = screened[i].second;
         }
     }
     if (best_ms < 0.f) return SINCOS_ECUDA;
