@@ -280,7 +280,10 @@ typedef enum {
     SINCOS_OP_BACKWARD = 1,
     SINCOS_OP_BATCHED = 2,
     SINCOS_OP_EXPI = 3,
-    SINCOS_OP_HUYGENS = 4   /* plan: block = threads per CTA, unroll = points per thread */
+    SINCOS_OP_HUYGENS = 4   /* plan: block = threads per CTA, unroll = points per thread
+                               (1, 2 or 4), vec_bytes = 16 for one binary32 operation per
+                               instruction, 32 for two sources per instruction on the
+                               packed FP32 pipe (same results) */
 } sincos_op;
 
 /* A launch configuration.  The paper's only tuning knob is its 2-way

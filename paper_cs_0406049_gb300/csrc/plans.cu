@@ -53,7 +53,7 @@ sincos_plan default_plan(int op, int dtype)
     // path; 16-bit outputs run faster on the 32-byte register path.
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
     if (op == SINCOS_OP_EXPI) return sincos_plan{512, 2, 1, 0};
-    if (op == SINCOS_OP_HUYGENS) return sincos_plan{256, 2, 8, 16};
+    if (op == SINCOS_OP_HUYGENS) return sincos_plan{256, 1, 8, 32};
     if (op == SINCOS_OP_BATCHED)
         return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
     return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
@@ -160,7 +160,8 @@ std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
     std::vector<sincos_plan> out;
     if (op == SINCOS_OP_HUYGENS) {  // CTA size and points per thread only
         for (int block : {128, 256, 512})
-            for (int pts : {1, 2, 4}) out.push_back(sincos_plan{block, pts, 8, 16});
+            for (int pts : {1, 2, 4})
+                for (int vec : {16, 32}) out.push_back(sincos_plan{block, pts, 8, vec});
         return out;
     }
     if (op != SINCOS_OP_BACKWARD)   // bulk path: one CTA per SM, CTA size only

@@ -26,7 +26,8 @@ def gpu_field(p, q, a, k, red):
 
 
 @pytest.mark.parametrize("plan", [(256, 2, 8, 16), (128, 1, 8, 16), (512, 4, 8, 16),
-                                  (256, 4, 8, 16)])
+                                  (256, 4, 8, 16), (256, 1, 8, 32), (128, 2, 8, 32),
+                                  (512, 4, 8, 32)])
 @pytest.mark.parametrize("red", ["compensated", "plain"])
 def test_huygens_ragged(cuda_lib, plan, red):
     with forced_plan("huygens", "f32", plan):
@@ -35,6 +36,28 @@ def test_huygens_ragged(cuda_lib, plan, red):
             p, q, a, k = pins.huygens_case(m=m, n=n, seed=m + n)
             want = oracle.huygens(p, q, a, k, red).view(np.float32)
             assert_f32_parity(gpu_field(p, q, a, k, red), want, f"huygens {plan} {red} {m}x{n}")
+
+
+@pytest.mark.parametrize("plan", [(256, 1, 8, 16), (256, 1, 8, 32), (128, 4, 8, 32)])
+@pytest.mark.parametrize("red", ["compensated", "plain"])
+def test_huygens_one_term_per_point(cuda_lib, plan, red):
+    """One source and 2^20 + 3 points: every output is a single term
+    w (a exp(i k r)), so each phase factor (and each packed pair of them) is
+    compared on its own, not inside a sum.  Distances from 1e-3 to 3e3 at
+    k = 37.7 put k r across 1.8e4 revolutions and every reduced angle."""
+    m = (1 << 20) + 3
+    rng = np.random.default_rng(17)
+    d = np.exp(rng.uniform(np.log(1e-3), np.log(3e3), m))
+    u = rng.standard_normal((m, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    p = tuple((d[:, None] * u)[:, i].astype(np.float32) for i in range(3))
+    q = tuple(np.array([v], np.float32) for v in (0.25, -0.5, 0.125))
+    a = np.array([0.75 - 1.25j], np.complex64)
+    k = float(np.float32(37.7))
+    with forced_plan("huygens", "f32", plan):
+        got = gpu_field(p, q, a, k, red)
+    want = oracle.huygens(p, q, a, k, red).view(np.float32)
+    assert_f32_parity(got, want, f"one-term huygens {plan} {red}")
 
 
 def test_huygens_diffraction_workload_sampled(cuda_lib):
