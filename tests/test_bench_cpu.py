@@ -68,3 +68,21 @@ def test_reference_arm_line():
     assert line["config"]["workload"] == "bandwidth_2p28"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_accuracy_statistics_of_known_errors():
+    """The Euclidean and amplitude errors of results with planted errors: an
+    exact pair gives zeros; s off by 3e-7 and c off by 4e-7 at x = 0 (s = 0,
+    c = 1) give a Euclidean error of 5e-7 and an amplitude error of 4e-7."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    x = np.zeros(4, np.float32)
+    st = bench.e1_stats(x, np.zeros(4), np.ones(4))
+    assert st["rms_euclid"] == 0.0 and st["max_euclid"] == 0.0 and st["max_amplitude"] == 0.0
+    s = np.array([0.0, 3e-7, 0.0, 0.0])
+    c = np.array([1.0, 1.0 + 4e-7, 1.0, 1.0])
+    st = bench.e1_stats(x, s, c)
+    assert abs(st["max_euclid"] - 5e-7) < 1e-15
+    assert abs(st["rms_euclid"] - 2.5e-7) < 1e-15          # sqrt(25e-14 / 4)
+    assert abs(st["max_amplitude"] - 4e-7) < 1e-13         # hypot(3e-7, 1 + 4e-7) - 1
