@@ -191,18 +191,20 @@ struct LaunchTimer {
         if (a) cudaEventDestroy(a);
         if (b) cudaEventDestroy(b);
     }
-    // Duration of one run of `launch` on `st` in milliseconds, or -1.
+    // Duration of `runs` back-to-back runs of `launch` on `st` in
+    // milliseconds per run, or -1.
     template <class F>
-    float once(F &&launch, cudaStream_t st)
+    float once(F &&launch, cudaStream_t st, int runs = 1)
     {
         if (!ok) return -1.f;
         cudaEventRecord(a, st);
-        if (launch() != SINCOS_OK) return -1.f;
+        for (int r = 0; r < runs; ++r)
+            if (launch() != SINCOS_OK) return -1.f;
         cudaEventRecord(b, st);
         float t = 0.f;
         if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&t, a, b) != cudaSuccess)
             return -1.f;
-        return t;
+        return t / (float)runs;
     }
 };
 
@@ -223,13 +225,16 @@ bool stream_is_capturing(cudaStream_t st)
 }
 
 // Two rounds.  The screen times every candidate (one warm-up run, median of
-// three); with a hundred candidates the single fastest median is often a
-// lucky one, so the few fastest are then timed again round-robin -- one run
-// of each per pass, so that a change of clock or of L2 state shifts them all
-// alike -- and the lowest median of those passes wins.
+// three single runs); with a hundred candidates the single fastest median is
+// often a lucky one, so the few fastest are then timed again round-robin --
+// one burst of back-to-back runs of each per pass, so that a change of clock
+// or of L2 state shifts them all alike, and so that what is timed is the
+// steady rate of repeated calls, launch gaps included -- and the lowest
+// median of those passes wins.
 constexpr int kScreenReps = 3;
 constexpr int kFinalists = 6;
 constexpr int kConfirmPasses = 9;
+constexpr int kConfirmBurst = 4;
 
 template <class F>
 int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F &&launch_with,
@@ -260,7 +265,8 @@ int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F
     std::vector<std::vector<float>> ms(screened.size());
     for (int pass = 0; pass < kConfirmPasses; ++pass)
         for (size_t i = 0; i < screened.size(); ++i) {
-            const float t = timer.once([&] { return launch_with(screened[i].second); }, st);
+            const float t =
+                timer.once([&] { return launch_with(screened[i].second); }, st, kConfirmBurst);
             if (t > 0.f) ms[i].push_back(t);
         }
     cudaStreamSynchronize(st);
