@@ -294,11 +294,18 @@ def time_flushed(torch, fn, steps: int, warmup: int, flush) -> list:
 def e1_stats(x: np.ndarray, s: np.ndarray, c: np.ndarray) -> dict:
     """The paper's accuracy statistics (Sec. Results): RMS and max of the
     Euclidean error sqrt(ds^2 + dc^2) against FP64 sin/cos, and the max
-    amplitude error |sqrt(s^2 + c^2) - 1|, all evaluated in FP64."""
+    amplitude error |sqrt(s^2 + c^2) - 1|, all evaluated in FP64.  The max
+    is given twice: against the binary32 angle, and against the reduced
+    angle the method sees, 2 pi fl(x K) with K = fl(1 / (2 * 3.1415926536))
+    (the difference is the rounding of x K)."""
     xd = x.astype(np.float64)
     sd, cd = s.astype(np.float64), c.astype(np.float64)
     e = np.hypot(sd - np.sin(xd), cd - np.cos(xd))
+    k32 = np.float32(1.0 / (2.0 * 3.1415926536))
+    a = 2.0 * np.pi * (np.asarray(x, np.float32) * k32).astype(np.float64)
+    e_red = np.hypot(sd - np.sin(a), cd - np.cos(a))
     return {"rms_euclid": float(np.sqrt(np.mean(e * e))), "max_euclid": float(e.max()),
+            "max_euclid_reduced_angle": float(e_red.max()),
             "max_amplitude": float(np.abs(np.hypot(sd, cd) - 1.0).max()), "sample": int(x.size)}
 
 

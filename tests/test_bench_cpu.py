@@ -80,9 +80,16 @@ def test_accuracy_statistics_of_known_errors():
     x = np.zeros(4, np.float32)
     st = bench.e1_stats(x, np.zeros(4), np.ones(4))
     assert st["rms_euclid"] == 0.0 and st["max_euclid"] == 0.0 and st["max_amplitude"] == 0.0
+    assert st["max_euclid_reduced_angle"] == 0.0          # fl(0 * K) = 0
     s = np.array([0.0, 3e-7, 0.0, 0.0])
     c = np.array([1.0, 1.0 + 4e-7, 1.0, 1.0])
     st = bench.e1_stats(x, s, c)
     assert abs(st["max_euclid"] - 5e-7) < 1e-15
     assert abs(st["rms_euclid"] - 2.5e-7) < 1e-15          # sqrt(25e-14 / 4)
     assert abs(st["max_amplitude"] - 4e-7) < 1e-13         # hypot(3e-7, 1 + 4e-7) - 1
+    # x = 1: the reduced angle 2 pi fl(K) differs from 1 by the rounding of K
+    k32 = float(np.float32(1.0 / (2.0 * 3.1415926536)))
+    a = 2 * np.pi * k32
+    st = bench.e1_stats(np.ones(1, np.float32), np.array([np.sin(a)]), np.array([np.cos(a)]))
+    assert st["max_euclid_reduced_angle"] == 0.0
+    assert abs(st["max_euclid"] - abs(2 * np.sin((a - 1.0) / 2))) < 1e-16   # chord of a - 1
