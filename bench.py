@@ -46,7 +46,7 @@ BYTES_PER_PAIR = 12            # 4 B angle read + 4 B sine + 4 B cosine written
 HUYGENS_OPS_PER_TERM = 41
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0      # only when the measured-peaks file is absent
-FWD_SOURCES = ["core.cuh", "bulk.cuh", "forward.cuh", "forward_f32.cu"]
+FWD_SOURCES = ["core.cuh", "core_x2.cuh", "bulk.cuh", "forward.cuh", "forward_f32.cu"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "ncu_forward_f32_bandwidth_2p28.md")
 
 

@@ -14,7 +14,8 @@
 // The packed instructions take no negated operands, so the steps whose
 // operands carry a sign (the differences of squares and the final products)
 // run as scalar instructions, where the sign is free.
-// Used by kernels bound by instruction issue rather than by memory.
+// Used by the Huygens kernel (bound by the FMA pipe) and by the bulk forward
+// kernel's binary32 tiles (shorter compute phase between memory stages).
 #pragma once
 
 #include "core.cuh"
