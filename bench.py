@@ -291,6 +291,49 @@ def time_flushed(torch, fn, steps: int, warmup: int, flush) -> list:
     return per
 
 
+def gpu_local_cpus(torch, dev: int) -> set:
+    """CPUs the kernel lists as local to the GPU's PCI function
+    (local_cpulist in sysfs), among those this process may run on; empty if
+    unknown."""
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        path = (f"/sys/bus/pci/devices/{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:"
+                f"{p.pci_device_id:02x}.0/local_cpulist")
+        with open(path) as f:
+            text = f.read().strip()
+    except (AttributeError, OSError):
+        return set()
+    return parse_cpulist(text) & os.sched_getaffinity(0)
+
+
+def parse_cpulist(text: str) -> set:
+    """A Linux CPU list ("0-3,8,10-11") as a set of CPU numbers."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def pinned_near_gpu(torch, dev: int, make):
+    """Run make() (which allocates page-locked host memory) on the CPUs local
+    to the GPU, so that the pages are placed on the GPU's NUMA node; returns
+    (make()'s result, a note of where it ran)."""
+    local = gpu_local_cpus(torch, dev)
+    saved = os.sched_getaffinity(0)
+    if not local or local == saved:
+        return make(), ("on the process's CPUs (already the GPU's local CPUs)" if local
+                        else "on the process's CPUs (GPU-local CPU list unknown)")
+    os.sched_setaffinity(0, local)
+    try:
+        return make(), f"on the {len(local)} CPUs local to the GPU"
+    finally:
+        os.sched_setaffinity(0, saved)
+
+
 def e1_stats(x: np.ndarray, s: np.ndarray, c: np.ndarray) -> dict:
     """The paper's accuracy statistics (Sec. Results): RMS and max of the
     Euclidean error sqrt(ds^2 + dc^2) against FP64 sin/cos, and the max
@@ -668,9 +711,11 @@ def run_ours(args, dist: Dist):
 
     e2e = None
     if not args.no_e2e:
-        xh = torch.from_numpy(x_np).pin_memory()
-        sh = torch.empty(n, dtype=torch.float32).pin_memory()
-        ch = torch.empty(n, dtype=torch.float32).pin_memory()
+        (xh, sh, ch), placed = pinned_near_gpu(
+            torch, torch.cuda.current_device(),
+            lambda: (torch.from_numpy(x_np).pin_memory(),
+                     torch.empty(n, dtype=torch.float32).pin_memory(),
+                     torch.empty(n, dtype=torch.float32).pin_memory()))
         ws = torch.empty(api.sincos_host_workspace_bytes("f32", 1 << 24), dtype=torch.uint8,
                          device="cuda")
         e_steps = max(3, min(args.steps, 10))
@@ -682,7 +727,8 @@ def run_ours(args, dist: Dist):
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": tot / e_steps,
                "path": "sincos_pairs_host on page-locked host buffers: one kernel reads x "
-                       "and writes s, c across NVLink-C2C (zero-copy)"}
+                       "and writes s, c across NVLink-C2C (zero-copy)",
+               "host_buffers_pinned": placed}
         del xh, sh, ch, ws
 
     ext = None

@@ -93,3 +93,11 @@ def test_accuracy_statistics_of_known_errors():
     st = bench.e1_stats(np.ones(1, np.float32), np.array([np.sin(a)]), np.array([np.cos(a)]))
     assert st["max_euclid_reduced_angle"] == 0.0
     assert abs(st["max_euclid"] - abs(2 * np.sin((a - 1.0) / 2))) < 1e-16   # chord of a - 1
+
+
+def test_cpulist_parsing():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()
