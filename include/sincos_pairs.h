@@ -320,8 +320,10 @@ int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan);
 
 /* Time every candidate plan on the caller's own buffers (writes s and c; x
  * must not alias them), store the fastest for this (op, dtype, n bucket) and
- * return it in *best.  Synchronizes `stream`.  Must not be called while
- * `stream` is captured. */
+ * return it in *best.  Timing: every candidate as the median of three single
+ * launches, then the six fastest round-robin over nine passes of four
+ * back-to-back launches each; the lowest median wins.  Synchronizes
+ * `stream`.  Must not be called while `stream` is captured. */
 int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_dtype,
                           int reduction, int coef, sincos_stream_t stream, sincos_plan *best);
 int sincos_autotune_backward(const float *gs, const float *gc, const float *s, const float *c,
