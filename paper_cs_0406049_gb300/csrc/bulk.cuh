@@ -77,8 +77,10 @@ __device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint
 }
 
 // Pairs of the E angles at element e of a staged input tile into the staged
-// output tiles (16-byte shared-memory accesses).
-template <int RED, int COEF, class OutT>
+// output tiles (16-byte shared-memory accesses).  PACK: two angles per packed
+// FP32 instruction where that applies (see below); the batched ring kernel
+// uses the scalar form.
+template <int RED, int COEF, class OutT, bool PACK = false>
 __device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *co, int e)
 {
     constexpr int E = Vec<OutT, 16>::E;
@@ -92,13 +94,13 @@ __device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *c
         in[q + 3] = v.w;
     }
     float sv[E], cv[E];
-    // Binary32 outputs with the normalized set: two angles per packed FP32
-    // instruction (core_x2.cuh, the same bits), which shortens the compute
-    // phase between stages (+0.4 % plain, +1.1 % compensated at 2^28).  For
-    // 16-bit outputs the packed form needs more registers than three CTAs of
-    // 512 threads can share and loses (6066 against 6532 GB/s), so it stays
-    // scalar there.
-    if constexpr (COEF == COEF_NORMALIZED && sizeof(OutT) == 4) {
+    // Packed (the single-array kernel's binary32 tiles, normalized set): two
+    // angles per packed FP32 instruction (core_x2.cuh, the same bits), which
+    // shortens the compute phase between stages (+0.4 % plain, +1.1 %
+    // compensated at 2^28).  For 16-bit outputs the packed form needs more
+    // registers than three CTAs of 512 threads can share and loses (6066
+    // against 6532 GB/s); in the batched ring kernel it measured 0.85 % slower.
+    if constexpr (PACK && COEF == COEF_NORMALIZED && sizeof(OutT) == 4) {
 #pragma unroll
         for (int i = 0; i < E; i += 2) {
             float2 s2, c2;
@@ -191,7 +193,7 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
         OutT *co = cout + b * CH;
 #pragma unroll
         for (int j = 0; j < PER_THREAD; ++j)
-            bulk_tile_vec<RED, COEF, OutT>(xi, so, co, (j * NT + tid) * E);
+            bulk_tile_vec<RED, COEF, OutT, true>(xi, so, co, (j * NT + tid) * E);
         // Make the tile visible to the bulk-copy (async) proxy, then let one
         // thread store it and refill this input stage.
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
