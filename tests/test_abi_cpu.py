@@ -172,3 +172,34 @@ def test_misaligned_pointers_are_rejected(lib):
     best = _lib.sincos_plan()
     assert lib.sincos_autotune_pairs(A + 2, A + 4096, A + 8192, 8, 0, 0, 0, stream,
                                      ctypes.byref(best)) == _lib.EINVAL
+
+
+VALID_CACHE = ('{"version": 1, "plans": [\n'
+               '  {"device": "test device \\"q\\":1", "op": 0, "dtype": 1, "bucket": 29, '
+               '"block": 512, "unroll": 2, "ctas_per_sm": 2, "vec_bytes": 0},\n'
+               '  {"device": "test device:1", "op": 4, "dtype": 0, "bucket": 19, '
+               '"block": 256, "unroll": 1, "ctas_per_sm": 8, "vec_bytes": 32}\n]}\n')
+
+
+@pytest.mark.parametrize("text,want", [
+    (VALID_CACHE, "OK"),
+    ('{"version": 1, "plans": []}', "OK"),
+    ('{"version": 1}', "EINVAL"),                                     # no plans
+    ('{"plans": {}}', "EINVAL"),                                      # plans not a list
+    ('{"plans": [{"device": "d", "op": 0, "dtype": 0, "bucket": 3, '
+     '"block": 100, "unroll": 2, "ctas_per_sm": 1, "vec_bytes": 16}]}', "EINVAL"),  # bad plan
+    ('{"plans": [{"op": 0, "dtype": 0, "bucket": 3, "block": 256, "unroll": 2, '
+     '"ctas_per_sm": 1, "vec_bytes": 16}]}', "EINVAL"),              # no device
+    ('{"plans": [{"device": "d", "op": x}]}', "EINVAL"),              # not a number
+    ('{"plans": [{"device" "d"}]}', "EINVAL"),                        # no colon
+    ('{"plans": [{device: "d"}]}', "EINVAL"),                         # key not a string
+    ('{"plans": [{"device": "unterminated', "EINVAL"),                # truncated string
+    ('{"plans": [{"device": "d", "op": 0', "EINVAL"),                 # truncated object
+    ('', "EINVAL"),
+])
+def test_plan_cache_reader(lib, tmp_path, text, want):
+    """The plan-cache reader needs no GPU: valid files load, malformed or
+    truncated ones are refused with EINVAL (and nothing is read past the end)."""
+    path = tmp_path / "plans.json"
+    path.write_text(text)
+    assert lib.sincos_plan_cache_load(str(path).encode()) == getattr(_lib, want)
