@@ -494,11 +494,67 @@ def pin_huygens_edges(lib):
     assert np.all(np.abs(u - ref) <= bound)
 
 
+# ----------------------------------------------------------------------------
+# Threaded driver (the CPU-baseline timing and the all-inputs GPU comparison).
+# ----------------------------------------------------------------------------
+
+MT_SIZES = (0, 1, 2, 3, 17, 1000003, (1 << 20) + 5)
+MT_THREADS = (1, 2, 3, 7, 16, 33, 600)     # 600 is above the driver's clamp of 512
+
+
+def _mt_angles(n: int) -> np.ndarray:
+    """Angles where the two reductions and the two coefficient sets all give
+    different results: uniform on [-pi, pi), log-uniform magnitudes up to 1e5
+    with random signs, and the special values."""
+    rng = np.random.default_rng(31)
+    third = n // 3
+    mag = 10.0 ** rng.uniform(-3, 5, n - 2 * third)
+    x = np.concatenate([rng.uniform(-math.pi, math.pi, third),
+                        rng.uniform(-1e3, 1e3, third),
+                        mag * np.where(rng.random(mag.size) < 0.5, -1.0, 1.0)])
+    sp = np.float32([np.nan, np.inf, -np.inf, 0.0, -0.0, 2.0 ** 26, 1e-40, 0.5])
+    k = min(sp.size, n)
+    x = x.astype(np.float32)
+    x[:k] = sp[:k]
+    return x
+
+
+def pin_threaded_driver(lib, sizes=MT_SIZES, threads=MT_THREADS):
+    """The threaded driver gives, for every size and thread count (ragged
+    splits, threads without work, the clamp), exactly the bits of the
+    single-threaded forward for each reduction and coefficient set, writes
+    nothing outside [0, n), and stays within the method's error of FP64 at the
+    reduced angle."""
+    guard = 8
+    sentinel = np.uint32(0x7FC0DEAD)          # a NaN no result of the method carries
+    variants = [(r, cf) for r in ("plain", "compensated") for cf in ("normalized", "dagger")]
+    for n in sizes:
+        x = _mt_angles(n)
+        for red, cf in variants:
+            want_s, want_c = lib.sincos(x, reduction=red, coef=cf)
+            if n and red == "plain" and cf == "normalized":
+                fin = np.isfinite(x) & (np.abs(x) <= 4.0)
+                if fin.any():
+                    assert core_error(x[fin], want_s[fin], want_c[fin]).max() <= CORE_BOUND
+            for t in threads:
+                sb = np.full(n + 2 * guard, sentinel, np.uint32).view(np.float32)
+                cb = np.full(n + 2 * guard, sentinel, np.uint32).view(np.float32)
+                s, c = sb[guard:guard + n], cb[guard:guard + n]
+                used = lib.sincos_mt(x, s, c, reduction=red, coef=cf, threads=t)
+                assert 0 <= used <= min(t, 512), (n, t, used)
+                what = f"n={n} threads={t} {red}/{cf}"
+                for buf in (sb, cb):
+                    assert np.all(buf[:guard].view(np.uint32) == sentinel), what + ": wrote before"
+                    assert np.all(buf[guard + n:].view(np.uint32) == sentinel), what + ": wrote after"
+                assert np.array_equal(s.view(np.uint32), want_s.view(np.uint32)), what + ": s"
+                assert np.array_equal(c.view(np.uint32), want_c.view(np.uint32)), what + ": c"
+
+
 ALL_PINS = [
     pin_e1_normalized, pin_e2_dagger, pin_drift_correction, pin_bruteforce,
     pin_bruteforce_small_angles, pin_symmetry,
     pin_periodicity, pin_exact_at_whole_turns, pin_quarter_turns, pin_ties_to_even,
     pin_special_values, pin_plain_reduction_bound, pin_compensated, pin_bf16_rounding,
     pin_f16_rounding, pin_16bit_outputs, pin_backward, pin_huygens_fp64, pin_huygens_airy,
-    pin_huygens_edges,
+    pin_huygens_edges, pin_threaded_driver,
 ]

@@ -59,13 +59,19 @@ MUTATIONS = {
                             "ure = pr + ure;\n            uim = pi + uim;")],
     "huygens_dropped_dz": [("float r = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));",
                             "float r = sqrtf(fmaf(dy, dy, dx * dx));")],
+    # threaded driver: a split that drops each thread's last element, and the
+    # coefficient set passed where the reduction belongs
+    "mt_split_drops_last": [("job[t].hi = n * (t + 1) / nthreads;",
+                             "job[t].hi = n * (t + 1) / nthreads - 1;")],
+    "mt_coef_as_reduction": [("job[t].reduction = reduction; job[t].coef = coef;",
+                              "job[t].reduction = coef; job[t].coef = coef;")],
 }
 
 # cheapest first; the expensive statistics run only if nothing cheaper fails
 PIN_ORDER = [
     pins.pin_special_values, pins.pin_symmetry, pins.pin_ties_to_even,
     pins.pin_exact_at_whole_turns, pins.pin_quarter_turns, pins.pin_periodicity,
-    pins.pin_backward, pins.pin_bf16_rounding, pins.pin_f16_rounding,
+    pins.pin_backward, pins.pin_threaded_driver, pins.pin_bf16_rounding, pins.pin_f16_rounding,
     pins.pin_16bit_outputs, pins.pin_compensated, pins.pin_plain_reduction_bound,
     pins.pin_drift_correction,
     functools.partial(pins.pin_e1_normalized, n=1 << 22),
