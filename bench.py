@@ -696,6 +696,9 @@ def run_ours(args, dist: Dist):
         launches = api.sincos_launch_count() - launches0 - args.warmup
     if sampler:
         sampler.stop()
+    # bounded waits in the kernels that gave up (read after the timed region:
+    # the read synchronizes the device)
+    wait_timeouts = int(api.sincos_device_wait_timeouts())
     max_ms = dist.max(total_ms)
     value = aggregate_value(dist.world, n, args.steps, max_ms)
     kernel_ms = statistics.mean(per)
@@ -748,6 +751,7 @@ def run_ours(args, dist: Dist):
         ext["differentiation_2p26"]["backward_vs_forward_gbs"] = \
             ext["differentiation_2p26"]["gbs"] / achieved
 
+    wait_timeouts += int(api.sincos_device_wait_timeouts())
     if dist.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
@@ -774,6 +778,7 @@ def run_ours(args, dist: Dist):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
+            "wait_timeouts": wait_timeouts,
             "clocks": clocks,
             "impl": "ours",
         }
@@ -781,6 +786,10 @@ def run_ours(args, dist: Dist):
             line["extras"] = ext
         print(json.dumps(line), flush=True)
     dist.close()
+    if wait_timeouts:
+        sys.stderr.write(f"bench: {wait_timeouts} bounded waits gave up inside the kernels; "
+                         "some launches stopped early and the numbers above are not valid\n")
+        raise SystemExit(3)
 
 
 def main():

@@ -59,7 +59,8 @@ typedef enum {
     SINCOS_EOVERLAP = -2,     /* forbidden overlap between input and output arrays     */
     SINCOS_ECUDA = -3,        /* a CUDA runtime call failed; see sincos_last_error()  */
     SINCOS_EUNSUPPORTED = -4, /* the device is not an sm_103 GPU, or a size limit hit  */
-    SINCOS_ECAPTURE = -5      /* the call would allocate while its stream is captured  */
+    SINCOS_ECAPTURE = -5      /* the call would allocate or do first-use set-up while
+                                 its stream is being captured                        */
 } sincos_status;
 
 /* Output element type.  BF16 and F16 results are the binary32 result rounded
@@ -220,12 +221,20 @@ int sincos_batched_release(void);
  *   Arguments, layout, results and errors are those of sincos_batched_ex;
  *   count > SINCOS_NOALLOC_MAX_SEGMENTS returns SINCOS_EUNSUPPORTED before
  *   anything is enqueued.
+ *   Only register plans (vec_bytes 16 or 32: the default for 16-bit outputs,
+ *   or a plan set or tuned for binary32) use the array.  Bulk plans
+ *   (vec_bytes 0, the binary32 default) run the ring kernel, which schedules
+ *   itself and touches no scratch; sincos_batched_ex allocates nothing for
+ *   them either.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before capturing any stream into a graph.
- *   All calls share the one array: calls whose work can overlap on the GPU
- *   (different streams without ordering between them) race and give wrong
- *   results.  Order them on one stream, or use sincos_batched instead.
+ *   (cudaGetSymbolAddress) with that device current, which may load the
+ *   library's device code onto the GPU; make that first call before
+ *   capturing any stream into a graph.  A first call on a stream that is
+ *   being captured returns SINCOS_ECAPTURE and enqueues nothing.
+ *   All calls share the one array: calls under register plans whose work can
+ *   overlap on the GPU (different streams without ordering between them)
+ *   race and give wrong results.  Order them on one stream, or use
+ *   sincos_batched instead.
  *   Each call rewrites every scratch entry it reads, so the contents left by
  *   an earlier call do not matter. */
 #define SINCOS_NOALLOC_MAX_SEGMENTS 65536
@@ -359,15 +368,17 @@ const char *sincos_strerror(int status);
 /* Text of the last failed CUDA call on this host thread ("" if none). */
 const char *sincos_last_error(void);
 /* Bounded waits inside bulk-path kernels that gave up (an mbarrier that did
- * not complete within its iteration limit) on the current device since the
- * previous call; the count is cleared by reading it.  Nonzero means a launch
- * stopped early and its outputs are incomplete.  Synchronizes the device. */
+ * not complete within one second of wall-clock time) on the current device
+ * since the previous call; the count is cleared by reading it.  Nonzero means
+ * a launch stopped early and its outputs are incomplete (each thread that
+ * gave up counts once).  Synchronizes the device. */
 uint32_t sincos_device_wait_timeouts(void);
 /* Self-test of the timeout path (the paper has no counterpart): one CTA waits
- * on a barrier nothing ever completes, giving up after `spins` polls
- * (1 .. 2^20) as the bulk kernels do; the next sincos_device_wait_timeouts()
- * then reports one more timeout.  No fault, no trap: the device stays usable. */
-int sincos_selftest_wait_timeout(uint32_t spins, sincos_stream_t stream);
+ * on a barrier nothing ever completes, giving up after limit_us microseconds
+ * (1 .. 10^6) as the bulk kernels do after one second; the next
+ * sincos_device_wait_timeouts() then reports one more timeout.  No fault, no
+ * trap: the device stays usable. */
+int sincos_selftest_wait_timeout(uint32_t limit_us, sincos_stream_t stream);
 /* Kernel launches this library has enqueued since load (all threads); a
  * graph replay counts the kernels in the graph. */
 uint64_t sincos_launch_count(void);

@@ -129,9 +129,9 @@ sincos_plan fit_plan(const void *kernel, const sincos_plan &plan, int *per_sm)
 }
 
 // One CTA waits on an mbarrier that nothing ever arrives on, with the given
-// spin limit, exactly as the bulk kernels wait on their stages; the wait gives
+// time limit, exactly as the bulk kernels wait on their stages; the wait gives
 // up and counts a timeout.  Exercises the timeout path without a fault.
-__global__ void k_selftest_wait(unsigned spins)
+__global__ void k_selftest_wait(unsigned long long limit_ns)
 {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
@@ -139,7 +139,7 @@ __global__ void k_selftest_wait(unsigned spins)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&bar), 0u, spins))
+    if (threadIdx.x == 0 && !mbar_wait_bounded(smem_addr(&bar), 0u, limit_ns))
         atomicAdd(&g_bulk_wait_timeouts, 1u);
 }
 
@@ -214,7 +214,8 @@ const char *sincos_strerror(int status)
     case SINCOS_EOVERLAP: return "input and output arrays overlap in a way that is not allowed";
     case SINCOS_ECUDA: return "a CUDA runtime call failed (see sincos_last_error)";
     case SINCOS_EUNSUPPORTED: return "unsupported device or configuration";
-    case SINCOS_ECAPTURE: return "the call would allocate while its stream is being captured";
+    case SINCOS_ECAPTURE:
+        return "the call would allocate or do first-use set-up while its stream is being captured";
     default: return "unknown status";
     }
 }
@@ -228,13 +229,13 @@ uint32_t sincos_device_wait_timeouts(void)
            take_timeouts_expi() + take_bulk_wait_timeouts_here();
 }
 
-int sincos_selftest_wait_timeout(uint32_t spins, sincos_stream_t stream)
+int sincos_selftest_wait_timeout(uint32_t limit_us, sincos_stream_t stream)
 {
-    if (spins == 0 || spins > (1u << 20)) return SINCOS_EINVAL;
+    if (limit_us == 0 || limit_us > 1000000u) return SINCOS_EINVAL;
     const DeviceInfo *dev = nullptr;
     const int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
-    k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(spins);
+    k_selftest_wait<<<1, 32, 0, (cudaStream_t)stream>>>(1000ull * limit_us);
     return check_launch("wait self-test launch");
 }
 

@@ -3,6 +3,7 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "trace.h"
 #include "internal.h"
@@ -35,6 +36,26 @@ int validate(const sincos_seg *segs, const int64_t *lens, int count, int dtype, 
         return SINCOS_EINVAL;
     if (count > 0 && (!segs || !lens)) return SINCOS_EINVAL;
     if (count > 0 && (!aligned_to(segs, 8) || !aligned_to(lens, 8))) return SINCOS_EINVAL;
+    return SINCOS_OK;
+}
+
+// Kernel nodes of a captured graph.
+int graph_kernel_nodes(cudaGraph_t graph, int *kernels)
+{
+    size_t nn = 0;
+    cudaError_t e = cudaGraphGetNodes(graph, nullptr, &nn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphGetNodes");
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphGetNodes");
+    int k = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        e = cudaGraphNodeGetType(nodes[i], &t);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphNodeGetType");
+        if (t == cudaGraphNodeTypeKernel) ++k;
+    }
+    *kernels = k;
     return SINCOS_OK;
 }
 
@@ -166,7 +187,10 @@ int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int
         const cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
         if (rc == SINCOS_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
         // Captured kernels are not launches; replays are counted instead.
-        if (rc == SINCOS_OK) count_launches((uint64_t)0 - 2u);
+        // launch_batched counted each kernel it enqueued (one for the ring
+        // plan, two for register plans), and each is one kernel node.
+        if (rc == SINCOS_OK) rc = graph_kernel_nodes(g->graph, &g->launches);
+        if (rc == SINCOS_OK) count_launches((uint64_t)0 - (uint64_t)g->launches);
     } else {
         rc = cuda_fail(e, "cudaStreamBeginCapture");
     }
@@ -179,7 +203,6 @@ int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int
         sincos_batched_graph_destroy(g);
         return rc;
     }
-    g->launches = 2;
     *out = g;
     return SINCOS_OK;
 }

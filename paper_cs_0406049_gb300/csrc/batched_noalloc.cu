@@ -25,8 +25,10 @@ namespace sincos_gb300 {
 namespace {
 
 // The batched schedule (tile prefix of up to SINCOS_NOALLOC_MAX_SEGMENTS
-// segments, then the per-CTA starts; see batched.cuh).  Every call writes all
-// the entries it later reads, so nothing needs clearing between calls.
+// segments, then the per-CTA starts; see batched.cuh).  Only register plans
+// (vec_bytes 16 or 32) use it; the ring kernel of bulk plans schedules itself
+// and touches no scratch.  Every call writes all the entries it later reads,
+// so nothing needs clearing between calls.
 __device__ __align__(256) int64_t g_noalloc_prefix[SINCOS_NOALLOC_MAX_SEGMENTS + 1 +
                                                    2 * (kMaxBatchedCtas + 1)];
 
@@ -34,13 +36,26 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 int64_t *g_noalloc_ptr[kMaxDevices] = {nullptr};
 
+bool stream_is_capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 // Device address of g_noalloc_prefix on the current device (looked up on the
-// first call for that device).
-int noalloc_scratch(int dev, int64_t **out)
+// first call for that device).  The lookup may load the library's device
+// code onto the GPU, which must not happen inside a stream capture: a first
+// call on a capturing stream is refused with SINCOS_ECAPTURE.
+int noalloc_scratch(int dev, cudaStream_t st, int64_t **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return SINCOS_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
+        if (stream_is_capturing(st)) return SINCOS_ECAPTURE;
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_prefix);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress (no-alloc scratch)");
@@ -71,7 +86,7 @@ extern "C" int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *len
     int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;
     int64_t *prefix = nullptr;
-    rc = noalloc_scratch(dev->ordinal, &prefix);
+    rc = noalloc_scratch(dev->ordinal, (cudaStream_t)stream, &prefix);
     if (rc != SINCOS_OK) return rc;
     const sincos_plan plan = plan_for(*dev, SINCOS_OP_BATCHED, out_dtype, count);
     return launch_batched(segs, lens, count, out_dtype, reduction, coef, prefix, plan, *dev,

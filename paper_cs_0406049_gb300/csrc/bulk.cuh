@@ -26,7 +26,13 @@ namespace sincos_gb300 {
 
 constexpr int kBulkChunk = 8192;   // angles per stage (32 KB)
 constexpr int kBulkStages = 2;
-constexpr unsigned kBulkSpinLimit = 1u << 20;
+// A bounded wait gives up after this much wall-clock time (%globaltimer), far
+// beyond any healthy stage (a 32 KB copy takes microseconds), so a slow but
+// healthy copy on a busy GPU cannot trip it.  The poll count is capped too,
+// far beyond the time limit (each poll suspends in try_wait), so the loop
+// ends even if the timer were not to advance.
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;   // 1 s
+constexpr unsigned kBulkWaitPollCap = 1u << 28;
 
 // Per translation unit; each TU that launches bulk kernels reports its own.
 static __device__ unsigned int g_bulk_wait_timeouts = 0;
@@ -46,16 +52,35 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
-                                                  unsigned limit = kBulkSpinLimit)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (unsigned it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One potentially blocking test of the barrier's phase `parity`.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of the barrier for at most limit_ns of wall-clock
+// time; false if it gave up.  The clock is read only once the first test
+// has failed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kBulkWaitNs)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < kBulkWaitPollCap; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 >= limit_ns) return false;
     }
     return false;
 }

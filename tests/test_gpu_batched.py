@@ -118,21 +118,44 @@ def test_separate_tensors_mixed_alignment(cuda_lib, path):
         assert_f32_parity(as_np(cs[i]), want_c, f"seg {i} c")
 
 
-def test_graph_replay_bit_identical(cuda_lib):
+# kernels per batched call: the ring kernel alone, or the schedule kernel and
+# the tile kernel of a register plan
+GRAPH_CASES = {"default": (None, 1), "bulk256": (PATHS["bulk256"], 1),
+               "reg16": (PATHS["reg16"], 2), "reg32": (PATHS["reg32"], 2)}
+
+
+@pytest.mark.parametrize("case", sorted(GRAPH_CASES))
+def test_graph_replay_bit_identical(cuda_lib, case):
+    """The graph's results equal the oracle's on the first replay and the
+    first replay's bits on the second; creating the graph leaves the launch
+    counter where it was, and each replay adds the kernels the graph holds."""
+    plan, kernels = GRAPH_CASES[case]
     lens = EDGE_LENS * 3
+    if plan is None:       # whatever plan the library holds for this count now
+        kernels = 1 if api.sincos_plan_get("batched", "f32", len(lens))["vec_bytes"] == 0 else 2
     x, xt, s, c, offs = packed(lens, "f32", seed=3)
     segs, lens_t = api.segments(xt, s, c, offs, lens)
-    with api.BatchedGraph(segs, lens_t) as g:
+    ctx = forced_plan("batched", "f32", plan) if plan else None
+    if ctx:
+        ctx.__enter__()
+    try:
+        before = api.sincos_launch_count()
+        g = api.BatchedGraph(segs, lens_t)
+        assert api.sincos_launch_count() == before, "capturing counted launches"
+    finally:
+        if ctx:
+            ctx.__exit__(None, None, None)
+    with g:
         g.launch()
         torch.cuda.synchronize()
-        check_all(x, s, c, "f32", "plain", "normalized", "graph replay 1")
+        check_all(x, s, c, "f32", "plain", "normalized", f"graph replay 1 ({case})")
         first_s, first_c = as_np(s).copy(), as_np(c).copy()
         s.fill_(0)
         c.fill_(0)
         before = api.sincos_launch_count()
         g.launch()
         torch.cuda.synchronize()
-        assert api.sincos_launch_count() == before + 2
+        assert api.sincos_launch_count() == before + kernels
         assert np.array_equal(as_np(s).view(np.uint32), first_s.view(np.uint32))
         assert np.array_equal(as_np(c).view(np.uint32), first_c.view(np.uint32))
 

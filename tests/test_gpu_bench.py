@@ -36,4 +36,5 @@ def test_bench_line_has_the_contract_keys(cuda_lib):
     assert e2e["d2h_bytes_per_step"] == 8 * (1 << 28)
     assert 0 < e2e["value"] < line["value"]
     assert line["gpu_launches"] >= 50
+    assert line["wait_timeouts"] == 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(line["clocks"])
