@@ -46,6 +46,12 @@ BYTES_PER_PAIR = 12            # 4 B angle read + 4 B sine + 4 B cosine written
 HUYGENS_OPS_PER_TERM = 41
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0      # only when the measured-peaks file is absent
+E2E_ROUTES = {
+    "zero-copy": "sincos_pairs_host on page-locked, mapped host buffers: one kernel reads x "
+                 "and writes s, c across NVLink-C2C",
+    "pipeline": "sincos_pairs_host through the chunked copy pipeline: host -> device copy, "
+                "kernel, device -> host copy on three rotating streams",
+}
 FWD_SOURCES = ["core.cuh", "core_x2.cuh", "bulk.cuh", "forward.cuh", "forward_f32.cu"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "ncu_forward_f32_bandwidth_2p28.md")
 
@@ -273,6 +279,47 @@ def fp64_errors(x: np.ndarray, s: np.ndarray, c: np.ndarray) -> dict:
             "max_ulp_rel_ge_2m4": float((d[big] / ulp).max()), "sample": int(ok.sum())}
 
 
+def backward_fp64_errors(x, gs, gc, gx) -> dict:
+    """gx against the FP64 analytic gradient gs cos x - gc sin x of the same
+    binary32 inputs: max abs error, and the max relative to |gs| + |gc|."""
+    xd = x.astype(np.float64)
+    gsd, gcd = gs.astype(np.float64), gc.astype(np.float64)
+    ref = gsd * np.cos(xd) - gcd * np.sin(xd)
+    ok = np.isfinite(ref)
+    d = np.abs(gx.astype(np.float64)[ok] - ref[ok])
+    scale = np.abs(gsd[ok]) + np.abs(gcd[ok])
+    return {"max_abs": float(d.max()), "max_rel_to_abs_gs_plus_abs_gc": float((d / scale).max()),
+            "sample": int(ok.sum()), "reference": "FP64 gs*cos(x) - gc*sin(x)"}
+
+
+def huygens_fp64_errors(w, u, pts) -> dict:
+    """The Huygens sums of the points `pts` against an FP64 direct sum of
+    a_j exp(i k r) / r over the same binary32 coordinates and amplitudes:
+    max abs error, and the max relative to the point's sum of |a_j| / r."""
+    p = [v[pts].astype(np.float64) for v in w.p]
+    q = [v.astype(np.float64) for v in w.q]
+    a = w.a.astype(np.complex128)
+    k = float(np.float32(w.k))
+    r = np.sqrt((p[0][:, None] - q[0][None, :]) ** 2 + (p[1][:, None] - q[1][None, :]) ** 2 +
+                (p[2][:, None] - q[2][None, :]) ** 2)
+    ref = (a[None, :] * np.exp(1j * k * r) / r).sum(axis=1)
+    scale = (np.abs(a)[None, :] / r).sum(axis=1)
+    got = u[pts, 0].astype(np.float64) + 1j * u[pts, 1].astype(np.float64)
+    d = np.abs(got - ref)
+    return {"max_abs": float(d.max()), "max_rel_to_sum_abs_terms": float((d / scale).max()),
+            "sample": int(pts.size), "reference": "FP64 direct sum over all sources"}
+
+
+def batch_sample(offsets, lens, seed: int = 0) -> np.ndarray:
+    """Indices of the first and last 64 and 64 random angles of every array."""
+    rng = np.random.default_rng(seed)
+    idx = []
+    for off, n in zip(offsets, lens):
+        k = min(int(n), 64)
+        idx += [off + np.arange(k), off + n - k + np.arange(k), off + rng.integers(0, n, 64)]
+    return np.unique(np.concatenate(idx))
+
+
 def time_flushed(torch, fn, steps: int, warmup: int, flush) -> list:
     """Per-call device ms of fn with the L2 flushed before every call (a
     write of `flush`, larger than L2, outside the timed events)."""
@@ -462,26 +509,33 @@ def cpu_baseline(x: np.ndarray) -> dict:
 
 def cuda_libm_context(torch, x_np, x, s, c, dist, steps: int) -> dict:
     """CUDA's sincosf and __sincosf on the same 2^28 angles and buffers, for
-    context: GB/s and FP64 errors on a sample."""
+    context: GB/s and FP64 errors on a sample.  sincosf is timed under each
+    nvcc flag set of the context build (defaults, -use_fast_math, and the
+    -prec-div/-prec-sqrt/-ftz switches alone); __sincosf under the defaults."""
     import ctypes
     from paper_cs_0406049_gb300 import build as libbuild
-    lib = ctypes.CDLL(libbuild.build_context())
-    lib.context_libm_sincos.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                        ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
     out = {}
     n = x.numel()
     rng = np.random.default_rng(0)
     idx = rng.integers(0, n, 1 << 20)
     it = torch.from_numpy(idx).cuda()
-    for name, fast in (("sincosf", 0), ("__sincosf", 1)):
-        st = torch.cuda.current_stream().cuda_stream
-        run = lambda: lib.context_libm_sincos(x.data_ptr(), s.data_ptr(), c.data_ptr(), n, fast, st)
-        total, per, _ = time_loop(torch, run, steps, 3, dist)
-        ms = statistics.mean(per)
-        err = fp64_errors(x_np[idx], s[it].cpu().numpy().astype(np.float64),
-                          c[it].cpu().numpy().astype(np.float64))
-        out[name] = {"pairs_per_s": n / (ms * 1e-3), "gbs": 12 * n / (ms * 1e-3) / 1e9,
-                     "errors": err}
+    for variant, path in libbuild.build_context_all().items():
+        lib = ctypes.CDLL(path)
+        lib.context_libm_sincos.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+        cases = (("sincosf", 0), ("__sincosf", 1)) if variant == "default" else (("sincosf", 0),)
+        for name, fast in cases:
+            st = torch.cuda.current_stream().cuda_stream
+            run = lambda: lib.context_libm_sincos(x.data_ptr(), s.data_ptr(), c.data_ptr(), n,
+                                                  fast, st)
+            total, per, _ = time_loop(torch, run, steps, 3, dist)
+            ms = statistics.mean(per)
+            err = fp64_errors(x_np[idx], s[it].cpu().numpy().astype(np.float64),
+                              c[it].cpu().numpy().astype(np.float64))
+            key = name if variant == "default" else f"{name} [{variant}]"
+            out[key] = {"pairs_per_s": n / (ms * 1e-3), "gbs": 12 * n / (ms * 1e-3) / 1e9,
+                        "nvcc_flags": " ".join(libbuild.CONTEXT_VARIANTS[variant]) or "defaults",
+                        "errors": err}
     return out
 
 
@@ -506,10 +560,12 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     ms = statistics.median(per)
     api.sincos_pairs(xt, s, c)
     torch.cuda.synchronize()
+    s_np, c_np = s.cpu().numpy(), c.cpu().numpy()
     out["plain_2p20"] = {
         "pairs_per_s": x.size / (ms * 1e-3), "us_per_call": 1e3 * ms,
         "l2_flushed": True, "bound": "launch and ramp (12.6 MB: about 2 us of HBM time)",
-        "accuracy": e1_stats(x, s.cpu().numpy(), c.cpu().numpy()),
+        "errors": fp64_errors(x, s_np.astype(np.float64), c_np.astype(np.float64)),
+        "accuracy": e1_stats(x, s_np, c_np),
         "accuracy_paper": {"rms_euclid": 1.2e-7, "max_euclid": 4.8e-7, "max_amplitude": 1.8e-7,
                            "source": "Sec. Results, normalized set (domain not stated)"},
         "plan": api.sincos_plan_get("pairs", "f32", x.size)}
@@ -548,8 +604,11 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         api.sincos_autotune_expi(xt, z)
     total, per, _ = time_loop(torch, lambda: api.sincos_expi(xt, z), k, 3, dist)
     ms = statistics.mean(per)
+    zs = torch.view_as_real(z[idx]).cpu().numpy().astype(np.float64)
     out["expi_complex64_2p26"] = {"gbs": 12 * x.size / (ms * 1e-3) / 1e9, "ms": ms,
                                   "frac_of_peak": 12 * x.size / (ms * 1e-3) / 1e9 / peak,
+                                  "reduction": "plain",
+                                  "errors": fp64_errors(x[idx.cpu().numpy()], zs[:, 1], zs[:, 0]),
                                   "plan": api.sincos_plan_get("expi", "f32", x.size)}
     del z, xt
 
@@ -572,6 +631,8 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         sampler.stop()
     ms = statistics.mean(per)
     terms = m * nsrc
+    u_np = torch.view_as_real(u).cpu().numpy()
+    hy_err = huygens_fp64_errors(w, u_np, np.random.default_rng(0).choice(m, 256, replace=False))
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     max_mhz = measured_sm_max_mhz()
     achieved = terms * HUYGENS_OPS_PER_TERM / (ms * 1e-3) / 1e12
@@ -583,6 +644,7 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
                      "unit": "TFLOP32-ops/s", "frac": achieved / peak_alu,
                      "peak_kind": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz} MHz",
                      "ops_per_term": HUYGENS_OPS_PER_TERM},
+        "errors": hy_err,
         "clocks": clocks}
     del P, Q, A, u
 
@@ -602,6 +664,12 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     bwd = {"gbs": 20 * xt.numel() / (ms * 1e-3) / 1e9, "ms": ms,
            "plan": api.sincos_plan_get("backward", "f32", xt.numel())}
     bwd["frac_of_peak"] = bwd["gbs"] / peak
+    di = np.random.default_rng(0).integers(0, w.x.size, 1 << 20)
+    dit = torch.from_numpy(di).cuda()
+    bwd["errors"] = {
+        "forward": fp64_errors(w.x[di], s[dit].cpu().numpy().astype(np.float64),
+                               c[dit].cpu().numpy().astype(np.float64)),
+        "backward": backward_fp64_errors(w.x[di], w.gs[di], w.gc[di], gx[dit].cpu().numpy())}
     xg = xt.clone().requires_grad_(True)
 
     def fwd_bwd():
@@ -653,6 +721,11 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     total, per, _ = time_loop(torch, graph.replay, 10, 2, dist)
     bat["separate_launches_graph_gbs"] = bytes_ / (statistics.mean(per) * 1e-3) / 1e9
     del graph
+    bi = batch_sample(b.offsets, b.lens)
+    bit = torch.from_numpy(bi).cuda()
+    bat["errors"] = fp64_errors(b.angles[bi], s[bit].cpu().numpy().astype(np.float64),
+                                c[bit].cpu().numpy().astype(np.float64))
+    bat["errors"]["sample_kind"] = "first and last 64 and 64 random angles of every array"
     out["batching_4096"] = bat
     return out
 
@@ -725,12 +798,13 @@ def run_ours(args, dist: Dist):
         tot, per_e, _ = time_loop(torch, lambda: api.sincos_pairs_host(xh, sh, ch, ws), e_steps,
                                   2, dist)
         tot = dist.max(tot)
+        route = api.sincos_host_last_path()
         assert torch.equal(sh[:1024], s[:1024].cpu()), "host path differs from device path"
         e2e = {"value": dist.world * n * e_steps / (tot * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": tot / e_steps,
-               "path": "sincos_pairs_host on page-locked host buffers: one kernel reads x "
-                       "and writes s, c across NVLink-C2C (zero-copy)",
+               "path": route,
+               "path_note": E2E_ROUTES.get(route, route),
                "host_buffers_pinned": placed}
         del xh, sh, ch, ws
 

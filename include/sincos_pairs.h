@@ -171,14 +171,24 @@ int sincos_backward(const float *gs, const float *gc, const float *s, const floa
 /* One array of the batch: x has lens[i] floats; s and c have lens[i]
  * elements of the batch's output dtype.  All three are device pointers,
  * each aligned to its element type (4 bytes for x and binary32 outputs, 2
- * for 16-bit outputs).  The descriptors live on the device, so the library
- * cannot check them: a misaligned or invalid pointer in a descriptor is
- * undefined behaviour (the kernels may fault). */
+ * for 16-bit outputs).  The descriptors live on the device and are checked
+ * there, by the kernels, before any array is touched: an array with
+ * lens[i] > 0 and a null or misaligned x, s or c is skipped (its outputs are
+ * not written) and counted, see sincos_device_bad_segments(); the same check
+ * is available on the host as sincos_seg_check().  What no check can see is
+ * whether a non-null, aligned pointer addresses lens[i] valid elements of
+ * this device's memory; that remains the caller's responsibility. */
 typedef struct {
     const float *x;
     void *s;
     void *c;
 } sincos_seg;
+
+/* The check the batched kernels apply to one descriptor, on the host: OK
+ * when len <= 0, or when x, s and c are non-null, x is 4-byte aligned and s
+ * and c are aligned to out_dtype's size; SINCOS_EINVAL otherwise (also for a
+ * null seg or a bad dtype).  seg is a host pointer.  No paper counterpart. */
+int sincos_seg_check(const sincos_seg *seg, int64_t len, int out_dtype);
 
 /* The forward over `count` independent arrays: the method of Sec.
  * Methodology and Fig. 1 applied to each array (batching itself is not in
@@ -280,6 +290,18 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
                       sincos_stream_t stream);
 size_t sincos_host_workspace_bytes(int out_dtype, int64_t chunk_elems);
 
+/* The route the calling thread's most recent sincos_pairs_host call took:
+ * SINCOS_HOST_PATH_ZERO_COPY (one kernel on the mapped host buffers),
+ * SINCOS_HOST_PATH_PIPELINE (chunked copies through dev_ws), or
+ * SINCOS_HOST_PATH_NONE (no call yet on this thread, n == 0, or the call
+ * returned an error).  Data movement only; the paper has no counterpart. */
+typedef enum {
+    SINCOS_HOST_PATH_NONE = 0,
+    SINCOS_HOST_PATH_ZERO_COPY = 1,
+    SINCOS_HOST_PATH_PIPELINE = 2
+} sincos_host_path;
+int sincos_host_last_path(void);
+
 /* ------------------------------------------------------------------------ */
 /* Launch plans and the autotuner                                            */
 /* ------------------------------------------------------------------------ */
@@ -373,6 +395,12 @@ const char *sincos_last_error(void);
  * a launch stopped early and its outputs are incomplete (each thread that
  * gave up counts once).  Synchronizes the device. */
 uint32_t sincos_device_wait_timeouts(void);
+/* Batched arrays the kernels skipped because their descriptor failed the
+ * check of sincos_seg_check (lens[i] > 0 with a null or misaligned pointer),
+ * on the current device since the previous call; each skipped array of a
+ * call counts once, and reading clears the count.  Synchronizes the
+ * device. */
+uint32_t sincos_device_bad_segments(void);
 /* Self-test of the timeout path (the paper has no counterpart): one CTA waits
  * on a barrier nothing ever completes, giving up after limit_us microseconds
  * (1 .. 10^6) as the bulk kernels do after one second; the next

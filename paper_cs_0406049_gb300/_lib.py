@@ -19,6 +19,7 @@ RED_PLAIN, RED_COMPENSATED = 0, 1
 COEF_NORMALIZED, COEF_DAGGER = 0, 1
 OP_PAIRS, OP_BACKWARD, OP_BATCHED, OP_EXPI, OP_HUYGENS = 0, 1, 2, 3, 4
 NOALLOC_MAX_SEGMENTS = 65536
+HOST_PATH_NONE, HOST_PATH_ZERO_COPY, HOST_PATH_PIPELINE = 0, 1, 2
 
 
 class sincos_plan(ctypes.Structure):
@@ -54,6 +55,7 @@ SIGNATURES = {
     "sincos_batched_graph_destroy": (_INT, [_VP]),
     "sincos_pairs_host": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _SZ, _VP]),
     "sincos_host_workspace_bytes": (_SZ, [_INT, _I64]),
+    "sincos_host_last_path": (_INT, []),
     "sincos_plan_get": (_INT, [_INT, _INT, _I64, _PLANP]),
     "sincos_plan_set": (_INT, [_INT, _INT, _I64, _PLANP]),
     "sincos_autotune_pairs": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _PLANP]),
@@ -67,6 +69,8 @@ SIGNATURES = {
     "sincos_strerror": (ctypes.c_char_p, [_INT]),
     "sincos_last_error": (ctypes.c_char_p, []),
     "sincos_device_wait_timeouts": (ctypes.c_uint32, []),
+    "sincos_device_bad_segments": (ctypes.c_uint32, []),
+    "sincos_seg_check": (_INT, [ctypes.c_void_p, _I64, _INT]),
     "sincos_selftest_wait_timeout": (_INT, [ctypes.c_uint32, _VP]),
     "sincos_launch_count": (ctypes.c_uint64, []),
     "sincos_version": (_INT, []),

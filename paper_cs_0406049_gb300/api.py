@@ -288,6 +288,17 @@ def sincos_pairs_host(x_host: torch.Tensor, s_host: torch.Tensor, c_host: torch.
             _stream(stream, workspace.device)), "sincos_pairs_host")
 
 
+_HOST_PATHS = {_lib.HOST_PATH_NONE: "none", _lib.HOST_PATH_ZERO_COPY: "zero-copy",
+               _lib.HOST_PATH_PIPELINE: "pipeline"}
+
+
+def sincos_host_last_path() -> str:
+    """The route of this thread's last sincos_pairs_host call: "zero-copy"
+    (one kernel on the mapped host buffers), "pipeline" (chunked copies) or
+    "none"."""
+    return _HOST_PATHS[lib().sincos_host_last_path()]
+
+
 # -----------------------------------------------------------------------------
 # Plans and the autotuner
 # -----------------------------------------------------------------------------
@@ -363,6 +374,19 @@ def sincos_plan_cache_load(path: str) -> None:
 def sincos_device_wait_timeouts() -> int:
     """Bounded waits that gave up in bulk-path kernels since the last call."""
     return int(lib().sincos_device_wait_timeouts())
+
+
+def sincos_device_bad_segments() -> int:
+    """Batched arrays skipped for a null or misaligned descriptor since the
+    last call."""
+    return int(lib().sincos_device_bad_segments())
+
+
+def sincos_seg_check(x: int, s: int, c: int, length: int, out_dtype="f32") -> bool:
+    """The batched kernels' descriptor check on the host, for raw addresses."""
+    seg = _lib.sincos_seg(x, s, c)
+    return lib().sincos_seg_check(ctypes.byref(seg), int(length),
+                                  _DTYPES[_torch_dtype(out_dtype)]) == _lib.OK
 
 
 def sincos_launch_count() -> int:

@@ -26,7 +26,19 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsincos_gb300.so")
 CONTEXT_SRC = os.path.join(HERE, "context", "cuda_libm.cu")
-CONTEXT_LIB = os.path.join(HERE, "context", "libsincos_context.so")
+# The CUDA sincosf context kernels under three sets of nvcc floating-point
+# flags: the defaults; -use_fast_math (which also maps sincosf to the
+# __sincosf intrinsic); and the -prec-div / -prec-sqrt / -ftz switches of
+# fast math alone, without the intrinsic mapping.
+CONTEXT_VARIANTS = {
+    "default": [],
+    "use_fast_math": ["-use_fast_math"],
+    "prec_off_ftz": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+}
+
+
+def context_lib_path(variant: str = "default") -> str:
+    return os.path.join(HERE, "context", f"libsincos_context_{variant}.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + [
@@ -100,29 +112,38 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     return LIB
 
 
-def build_context(force: bool = False) -> str:
+def build_context(force: bool = False, variant: str = "default") -> str:
     """The CUDA sincosf / __sincosf comparison kernels (benchmark context only),
-    compiled with nvcc's default floating-point flags."""
-    tag_file = CONTEXT_LIB + ".srctag"
+    compiled with one of the CONTEXT_VARIANTS flag sets."""
+    flags = CONTEXT_VARIANTS[variant]
+    lib = context_lib_path(variant)
+    tag_file = lib + ".srctag"
     with open(CONTEXT_SRC, "rb") as f:
-        tag = hashlib.sha1(f.read() + " ".join(ARCH).encode()).hexdigest()[:16]
-    if not force and os.path.exists(CONTEXT_LIB) and os.path.exists(tag_file):
+        tag = hashlib.sha1(f.read() + " ".join(ARCH + flags).encode()).hexdigest()[:16]
+    if not force and os.path.exists(lib) and os.path.exists(tag_file):
         with open(tag_file) as f:
             if f.read().strip() == tag:
-                return CONTEXT_LIB
-    tmp = CONTEXT_LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, CONTEXT_SRC]
+                return lib
+    tmp = lib + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-O3", *flags, "-Xcompiler", "-fPIC", "-shared", "-o", tmp, CONTEXT_SRC]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"nvcc failed on cuda_libm.cu:\n{r.stdout}{r.stderr}")
-    os.replace(tmp, CONTEXT_LIB)
+        raise RuntimeError(f"nvcc failed on cuda_libm.cu ({variant}):\n{r.stdout}{r.stderr}")
+    os.replace(tmp, lib)
     with open(tag_file, "w") as f:
         f.write(tag)
-    return CONTEXT_LIB
+    return lib
+
+
+def build_context_all(force: bool = False) -> dict:
+    """Every context variant, compiled in parallel; {variant: library path}."""
+    with ThreadPoolExecutor(max_workers=len(CONTEXT_VARIANTS)) as ex:
+        paths = list(ex.map(lambda v: build_context(force, v), CONTEXT_VARIANTS))
+    return dict(zip(CONTEXT_VARIANTS, paths))
 
 
 if __name__ == "__main__":
     p = build(force="--force" in sys.argv, verbose=True,
               ptxas_verbose="--ptxas-verbose" in sys.argv)
     print(p)
-    print(build_context(force="--force" in sys.argv))
+    print(build_context_all(force="--force" in sys.argv))

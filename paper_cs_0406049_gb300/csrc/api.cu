@@ -6,6 +6,7 @@
 #include <unordered_map>
 
 #include "bulk.cuh"
+#include "seg_check.h"
 #include "trace.h"
 #include "internal.h"
 
@@ -227,6 +228,19 @@ uint32_t sincos_device_wait_timeouts(void)
     return take_timeouts_forward_f32() + take_timeouts_forward_bf16() + take_timeouts_forward_f16() +
            take_timeouts_batched_f32() + take_timeouts_batched_bf16() + take_timeouts_batched_f16() +
            take_timeouts_expi() + take_bulk_wait_timeouts_here();
+}
+
+uint32_t sincos_device_bad_segments(void)
+{
+    return take_bad_segments_batched_f32() + take_bad_segments_batched_bf16() +
+           take_bad_segments_batched_f16();
+}
+
+int sincos_seg_check(const sincos_seg *seg, int64_t len, int out_dtype)
+{
+    if (!seg || !valid_dtype(out_dtype)) return SINCOS_EINVAL;
+    return seg_usable(seg->x, seg->s, seg->c, len, (unsigned)dtype_size(out_dtype))
+               ? SINCOS_OK : SINCOS_EINVAL;
 }
 
 int sincos_selftest_wait_timeout(uint32_t limit_us, sincos_stream_t stream)

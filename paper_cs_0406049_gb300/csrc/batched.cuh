@@ -48,10 +48,14 @@ __global__ void k_batched_prefix(const sincos_seg *segs, const int64_t *lens, in
     int64_t *first_seg = first_tile + grid + 1;
     __shared__ int64_t wa[32], wb[32];
 
+    // An array whose descriptor fails seg_ok gets no tiles (it is skipped);
+    // pass 2 counts it once.
     int64_t mine = 0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        const int64_t ne = lens[i] > 0 ? lens[i] : 0;
-        mine += ce * ne + ct * seg_tiles(ne, seg_head<OutT, W>(segs[i]), tile);
+        const sincos_seg d = segs[i];
+        int64_t ne = lens[i] > 0 ? lens[i] : 0;
+        if (!seg_ok<OutT>(d, ne)) ne = 0;
+        mine += ce * ne + ct * seg_tiles(ne, seg_head<OutT, W>(d), tile);
     }
     int64_t zero = 0, all = 0, unused = 0;
     cta_scan2(mine, zero, wa, wb, &all, &unused);
@@ -63,8 +67,13 @@ __global__ void k_batched_prefix(const sincos_seg *segs, const int64_t *lens, in
         int64_t nt = 0, nw = 0;
         int h = -1;
         if (i < count) {
-            const int64_t ne = lens[i] > 0 ? lens[i] : 0;
-            h = seg_head<OutT, W>(segs[i]);
+            const sincos_seg d = segs[i];
+            int64_t ne = lens[i] > 0 ? lens[i] : 0;
+            if (!seg_ok<OutT>(d, ne)) {
+                atomicAdd(&g_bad_segments, 1u);
+                ne = 0;
+            }
+            h = seg_head<OutT, W>(d);
             nt = seg_tiles(ne, h, tile);
             nw = ce * ne + ct * nt;
         }

@@ -6,8 +6,32 @@
 #include "bulk.cuh"
 #include "core.cuh"
 #include "internal.h"
+#include "seg_check.h"
 
 namespace sincos_gb300 {
+
+// Arrays skipped because their descriptor failed seg_usable, per translation
+// unit (each batched TU reports its own; a read clears it).
+static __device__ unsigned int g_bad_segments = 0;
+
+// seg_usable for a descriptor of the batch's output type.
+template <class OutT>
+__device__ __forceinline__ bool seg_ok(const sincos_seg &d, int64_t len)
+{
+    return seg_usable(d.x, d.s, d.c, len, (unsigned)sizeof(OutT));
+}
+
+// Reads and clears this translation unit's skipped-array counter.
+static inline unsigned take_bad_segments_here()
+{
+    unsigned v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bad_segments, sizeof v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaMemcpyToSymbol(g_bad_segments, &zero, sizeof zero);
+    return v;
+}
 
 // Where a segment's vector grid starts: the element h at which x, s and c
 // all start a 128-byte line, or failing that are W-byte vector aligned, or -1

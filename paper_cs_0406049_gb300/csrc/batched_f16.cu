@@ -11,5 +11,6 @@ int launch_batched_f16(const sincos_seg *segs, const int64_t *lens, int count, i
 }
 
 unsigned take_timeouts_batched_f16() { return take_bulk_wait_timeouts_here(); }
+unsigned take_bad_segments_batched_f16() { return take_bad_segments_here(); }
 
 }  // namespace sincos_gb300

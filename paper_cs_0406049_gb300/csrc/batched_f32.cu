@@ -22,5 +22,6 @@ int launch_batched(const sincos_seg *segs, const int64_t *lens, int count, int d
 }
 
 unsigned take_timeouts_batched_f32() { return take_bulk_wait_timeouts_here(); }
+unsigned take_bad_segments_batched_f32() { return take_bad_segments_here(); }
 
 }  // namespace sincos_gb300

@@ -92,12 +92,14 @@ __device__ __forceinline__ void consumer_sync(int nt)
 }
 
 // Metadata of segment `seg` in one producer lane (an empty slot past count).
+// ok: the descriptor passes seg_ok (else the producer skips the segment).
 struct SegMeta {
     const float *x;
     void *s;
     void *c;
     int64_t len, nt;
     int h;
+    bool ok;
 };
 
 template <class OutT>
@@ -113,11 +115,13 @@ __device__ __forceinline__ SegMeta load_seg_meta(const sincos_seg *segs, const i
         m.len = lens[seg] > 0 ? lens[seg] : 0;
         m.h = seg_head<OutT, 16>(d);
         m.nt = seg_tiles(m.len, m.h, kBulkChunk);
+        m.ok = seg_ok<OutT>(d, m.len);
     } else {
         m.x = nullptr;
         m.s = m.c = nullptr;
         m.len = m.nt = 0;
         m.h = -1;
+        m.ok = true;
     }
     return m;
 }
@@ -316,6 +320,15 @@ __device__ __forceinline__ void ring_producer(const sincos_seg *segs, const int6
                     const int c = (int)(seg - base);
                     nt = __shfl_sync(0xffffffffu, w.nt, c);
                     kend = seg == run.seg_b ? run.k_b : nt;
+                    // A descriptor that fails seg_ok keeps its place in the
+                    // schedule (the prologue reads lengths only) but is not
+                    // processed; the CTA that owns its first tile counts it.
+                    if (kt < kend && !__shfl_sync(0xffffffffu, (int)w.ok, c)) {
+                        if (kt == 0 && lane == 0) atomicAdd(&g_bad_segments, 1u);
+                        ++seg;
+                        kt = 0;
+                        continue;
+                    }
                     if (kt < kend) {
                         x = shfl_ptr(w.x, c);
                         so = shfl_ptr((OutT *)w.s, c);

@@ -21,6 +21,9 @@ namespace {
 constexpr int kSlots = 3;
 constexpr int kMaxDevices = 64;
 
+// The route the calling thread's last sincos_pairs_host call took.
+thread_local int g_last_path = SINCOS_HOST_PATH_NONE;
+
 struct Pipe {
     bool ready = false;
     cudaStream_t st[kSlots] = {nullptr, nullptr, nullptr};
@@ -95,6 +98,7 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
                       sincos_stream_t stream)
 {
     SINCOS_TRACE("sincos_pairs_host");
+    g_last_path = SINCOS_HOST_PATH_NONE;
     if (n < 0 || !valid_dtype(out_dtype) || !valid_reduction(reduction) || !valid_coef(coef))
         return SINCOS_EINVAL;
     if (n == 0) return SINCOS_OK;
@@ -121,8 +125,10 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
             if (o == (const void *)x_host && out_dtype == SINCOS_F32) in_place = true;
             else return SINCOS_EOVERLAP;
         }
-        return launch_forward((const float *)xd, sd, cd, n, out_dtype, reduction, coef, in_place,
-                              kZeroCopyPlan, *dev, user);
+        rc = launch_forward((const float *)xd, sd, cd, n, out_dtype, reduction, coef, in_place,
+                            kZeroCopyPlan, *dev, user);
+        if (rc == SINCOS_OK) g_last_path = SINCOS_HOST_PATH_ZERO_COPY;
+        return rc;
     }
 
     Pipe *pipe = nullptr;
@@ -161,7 +167,10 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
         if (e == cudaSuccess) e = cudaStreamWaitEvent(user, pipe->done[k], 0);
         if (e != cudaSuccess) return cuda_fail(e, "host path ordering before the caller's stream");
     }
+    g_last_path = SINCOS_HOST_PATH_PIPELINE;
     return SINCOS_OK;
 }
+
+int sincos_host_last_path(void) { return g_last_path; }
 
 }  // extern "C"

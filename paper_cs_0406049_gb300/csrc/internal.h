@@ -87,6 +87,11 @@ unsigned take_timeouts_batched_f32();
 unsigned take_timeouts_batched_bf16();
 unsigned take_timeouts_batched_f16();
 unsigned take_timeouts_expi();
+// Batched arrays skipped for a descriptor that failed seg_usable, per
+// translation unit (each read clears the count).
+unsigned take_bad_segments_batched_f32();
+unsigned take_bad_segments_batched_bf16();
+unsigned take_bad_segments_batched_f16();
 
 // Kernel launchers.  Arguments are already validated; they enqueue on `st`
 // and return a status.

@@ -117,6 +117,7 @@ def test_host_path_validation(lib):
     assert lib.sincos_pairs_host(A, A + 4096, A + 8192, 8, 0, 0, 0, ws + 4, 1 << 20, None) == _lib.EINVAL
     assert lib.sincos_pairs_host(A, A + 4096, A + 8192, 8, 0, 0, 0, ws, 64, None) == _lib.EINVAL
     assert lib.sincos_pairs_host(A, A + 4096, A + 4100, 8, 0, 0, 0, ws, 1 << 20, None) == _lib.EOVERLAP
+    assert lib.sincos_host_last_path() == _lib.HOST_PATH_NONE     # refused calls took no route
     assert lib.sincos_host_workspace_bytes(0, 64) == 3 * 64 * 12
     assert lib.sincos_host_workspace_bytes(1, 65) == 3 * 128 * 8
     assert lib.sincos_host_workspace_bytes(5, 64) == 0
@@ -203,3 +204,34 @@ def test_plan_cache_reader(lib, tmp_path, text, want):
     path = tmp_path / "plans.json"
     path.write_text(text)
     assert lib.sincos_plan_cache_load(str(path).encode()) == getattr(_lib, want)
+
+
+def test_seg_check_every_alignment(lib):
+    """The descriptor check the batched kernels apply, on the host: for every
+    combination of byte offsets 0..7 of x, s and c, null pointers, each output
+    dtype and lengths around zero, a descriptor passes exactly when its length
+    is <= 0 or all three pointers are non-null with x on a 4-byte and s, c on
+    an element boundary of the output dtype."""
+    base = 1 << 24
+    size = {_lib.F32: 4, _lib.BF16: 2, _lib.F16: 2}
+    seg = _lib.sincos_seg()
+    checked = 0
+    for dt, osz in size.items():
+        for length in (-7, -1, 0, 1, 3, 1 << 40):
+            for ox in range(8):
+                for os_ in range(8):
+                    for oc in range(8):
+                        for nulls in range(8):
+                            x = 0 if nulls & 1 else base + ox
+                            s = 0 if nulls & 2 else 2 * base + os_
+                            c = 0 if nulls & 4 else 3 * base + oc
+                            seg.x, seg.s, seg.c = x, s, c
+                            want = length <= 0 or (
+                                nulls == 0 and ox % 4 == 0 and os_ % osz == 0 and oc % osz == 0)
+                            got = lib.sincos_seg_check(ctypes.byref(seg), length, dt)
+                            assert got == (_lib.OK if want else _lib.EINVAL), (dt, length, x, s, c)
+                            checked += 1
+    assert checked == 3 * 6 * 8 ** 4
+    assert lib.sincos_seg_check(None, 1, _lib.F32) == _lib.EINVAL
+    seg.x, seg.s, seg.c = base, base, base
+    assert lib.sincos_seg_check(ctypes.byref(seg), 1, 7) == _lib.EINVAL

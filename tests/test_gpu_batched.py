@@ -51,6 +51,7 @@ def test_edge_lengths(cuda_lib, dtype, red, coef, path):
         api.sincos_batched(segs, lens, dtype, red, coef)
     check_all(x, s, c, dtype, red, coef, f"batched {path} {dtype}")
     assert api.sincos_device_wait_timeouts() == 0
+    assert api.sincos_device_bad_segments() == 0
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
@@ -284,3 +285,23 @@ def test_ring_plan_captures_without_a_prior_call(cuda_lib):
         graph.replay()
     torch.cuda.synchronize()
     check_all(x, s, c, "f32", "plain", "normalized", "captured ring batch")
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_null_pointers_on_empty_arrays(cuda_lib, path):
+    """Arrays of length <= 0 may carry null pointers (they are never used):
+    the other arrays are exact and nothing is counted as skipped.  Only valid
+    descriptors are launched here; the skip of invalid ones is checked on the
+    host (the same predicate, tests/test_abi_cpu.py)."""
+    lens = [5000, 0, 17, -3, 8193, 0]
+    x, xt, s, c, offs = packed(lens, "f32", seed=6)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    segs = segs.view(-1, 3).clone()
+    for i, n in enumerate(lens):
+        if n <= 0:
+            segs[i] = 0
+    assert api.sincos_device_bad_segments() == 0
+    with forced_plan("batched", "f32", PATHS[path]):
+        api.sincos_batched(segs.view(-1), lens_t)
+    check_all(x, s, c, "f32", "plain", "normalized", f"null empties {path}")
+    assert api.sincos_device_bad_segments() == 0

@@ -27,6 +27,7 @@ def test_host_path_chunks(cuda_lib, dtype, pinned):
     ws = torch.empty(api.sincos_host_workspace_bytes(dtype, 100000), dtype=torch.uint8,
                      device="cuda")
     api.sincos_pairs_host(xh, sh, ch, ws, "compensated")
+    assert api.sincos_host_last_path() == ("zero-copy" if pinned else "pipeline")
     torch.cuda.synchronize()
     want_s, want_c = oracle.sincos(x, reduction="compensated", out=dtype)
     if dtype == "f32":
@@ -48,6 +49,7 @@ def test_host_path_mixed_memory_kinds(cuda_lib):
     ws = torch.empty(api.sincos_host_workspace_bytes("f32", 65536), dtype=torch.uint8,
                      device="cuda")
     api.sincos_pairs_host(xh, sh, ch, ws)
+    assert api.sincos_host_last_path() == "pipeline"
     torch.cuda.synchronize()
     want_s, want_c = oracle.sincos(x)
     assert_f32_parity(sh.numpy(), want_s, "mixed s")
@@ -64,6 +66,7 @@ def test_host_path_zero_copy_in_place_and_overlap(cuda_lib):
     ws = torch.empty(api.sincos_host_workspace_bytes("f32", 4096), dtype=torch.uint8,
                      device="cuda")
     api.sincos_pairs_host(buf, buf, ch, ws)
+    assert api.sincos_host_last_path() == "zero-copy"
     torch.cuda.synchronize()
     want_s, want_c = oracle.sincos(x)
     assert_f32_parity(buf.numpy(), want_s, "in-place s")
@@ -72,6 +75,7 @@ def test_host_path_zero_copy_in_place_and_overlap(cuda_lib):
     before = big.clone()
     with pytest.raises(RuntimeError):
         api.sincos_pairs_host(big[:n], big[1:], ch, ws)
+    assert api.sincos_host_last_path() == "none"
     torch.cuda.synchronize()
     assert torch.equal(big.view(torch.int32), before.view(torch.int32))   # bits: NaNs included
 
