@@ -67,6 +67,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="time the library's default plans instead of tuning each op first")
+    p.add_argument("--split", action="store_true",
+                   help="strong scaling: one 2^28-angle array cut into contiguous blocks of "
+                        "n/N angles, one per rank (default: weak scaling, 2^28 per rank)")
     return p.parse_args()
 
 
@@ -256,6 +259,13 @@ def vendor_peak(torch, achieved_gbs: float) -> dict:
     gbs = khz * 1e3 * bits / 8 * 2 / 1e9
     return {"peak_vendor": gbs, "frac_vendor": achieved_gbs / gbs,
             "peak_vendor_kind": f"memory clock {khz / 1e3:.0f} MHz x {bits}-bit bus x 2"}
+
+
+def shard_bounds(n: int, rank: int, world: int) -> tuple:
+    """Rank `rank`'s contiguous block [lo, hi) of an n-element array cut into
+    `world` blocks whose sizes differ by at most one; the blocks tile [0, n).
+    Every element is independent, so no rank needs another's data."""
+    return n * rank // world, n * (rank + 1) // world
 
 
 def aggregate_value(world: int, n_per_rank: int, steps: int, max_ms: float) -> float:
@@ -744,7 +754,10 @@ def run_ours(args, dist: Dist):
     dev_name = torch.cuda.get_device_name()
 
     x_np = workloads.bandwidth()
-    n = x_np.size
+    n_total = x_np.size
+    lo, hi = shard_bounds(n_total, dist.rank, dist.world) if args.split else (0, n_total)
+    x_np = np.ascontiguousarray(x_np[lo:hi])
+    n = x_np.size                       # this rank's angles
     x = torch.from_numpy(x_np).cuda()
     s = torch.empty_like(x)
     c = torch.empty_like(x)
@@ -773,7 +786,9 @@ def run_ours(args, dist: Dist):
     # the read synchronizes the device)
     wait_timeouts = int(api.sincos_device_wait_timeouts())
     max_ms = dist.max(total_ms)
-    value = aggregate_value(dist.world, n, args.steps, max_ms)
+    # whole-job pairs/s: the slowest rank's time bounds the job
+    value = (n_total * args.steps / (max_ms * 1e-3) if args.split
+             else aggregate_value(dist.world, n, args.steps, max_ms))
     kernel_ms = statistics.mean(per)
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_PAIR * n / (kernel_ms * 1e-3) / 1e9
@@ -800,7 +815,8 @@ def run_ours(args, dist: Dist):
         tot = dist.max(tot)
         route = api.sincos_host_last_path()
         assert torch.equal(sh[:1024], s[:1024].cpu()), "host path differs from device path"
-        e2e = {"value": dist.world * n * e_steps / (tot * 1e-3), "unit": UNIT,
+        e2e = {"value": (n_total if args.split else dist.world * n) * e_steps / (tot * 1e-3),
+               "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": tot / e_steps,
                "path": route,
@@ -830,12 +846,15 @@ def run_ours(args, dist: Dist):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": max_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong" if args.split else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "description": WORKLOAD_DESC, "n": n,
                        "out_dtype": "f32", "reduction": "plain", "coef": "normalized",
                        "plan": plan, "l2": "inputs larger than L2 (3.2 GB per step vs 129 MB)",
-                       "parallelism": f"independent {n}-angle arrays per GPU x{dist.world}",
+                       "parallelism": (f"one {n_total}-angle array in {dist.world} contiguous "
+                                       f"blocks, one per GPU, no collective on the data"
+                                       if args.split else
+                                       f"independent {n}-angle arrays per GPU x{dist.world}"),
                        "device": dev_name, "remeasured_for_clocks": remeasured},
             "gbs": achieved * dist.world,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -48,6 +48,77 @@ def test_two_ranks_take_the_slowest_time():
     assert out[0][2] == pytest.approx(2 * (1 << 28) * 20 / 20e-3)
 
 
+def _shard_worker(rank, world, port, n, q):
+    """One rank of the split (strong-scaling) data plane on the CPU: the
+    oracle stands in for the kernel on this rank's block of one seeded array;
+    the blocks travel to rank 0 only for the check (the product path has no
+    collective on the data)."""
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import numpy as np
+    import torch.distributed as dist
+
+    import bench
+    import oracle
+    from paper_cs_0406049_gb300 import workloads
+    d = bench.Dist(world)
+    d.init("gloo")
+    x = workloads.angles_uniform(n, -1000.0, 1000.0, seed=1)
+    lo, hi = bench.shard_bounds(n, d.rank, d.world)
+    s, c = oracle.sincos(x[lo:hi])
+    got = [None] * world
+    dist.all_gather_object(got, (d.rank, lo, hi, s.view(np.uint32).tobytes(),
+                                 c.view(np.uint32).tobytes()))
+    if d.rank == 0:
+        got.sort()
+        assert got[0][1] == 0 and got[-1][2] == n
+        for a, b in zip(got, got[1:]):
+            assert a[2] == b[1], "blocks leave a gap or overlap"
+        assert max(h - l for _, l, h, _, _ in got) - min(h - l for _, l, h, _, _ in got) <= 1
+        ws, wc = oracle.sincos(x)
+        s_all = np.frombuffer(b"".join(g[3] for g in got), np.uint32)
+        c_all = np.frombuffer(b"".join(g[4] for g in got), np.uint32)
+        assert np.array_equal(s_all, ws.view(np.uint32))
+        assert np.array_equal(c_all, wc.view(np.uint32))
+    d.barrier()
+    q.put(rank)
+    d.close()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_data_plane_over_ranks(world):
+    """bench.py --split cuts one array into contiguous per-rank blocks; over
+    gloo ranks on the CPU the blocks tile the array, differ in size by at most
+    one, and the per-rank results put together are the oracle's for the
+    whole array, bit for bit (n = 1000003, so the blocks are ragged)."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, 1000003, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    done = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert done == list(range(world))
+
+
+def test_shard_bounds_tile_the_array():
+    sys.path.insert(0, ROOT)
+    import bench
+    for n in (0, 1, 5, 1 << 28, (1 << 28) + 7):
+        for world in (1, 2, 3, 4, 8):
+            b = [bench.shard_bounds(n, r, world) for r in range(world)]
+            assert b[0][0] == 0 and b[-1][1] == n
+            assert all(b[i][1] == b[i + 1][0] for i in range(world - 1))
+            sizes = [h - l for l, h in b]
+            assert max(sizes) - min(sizes) <= 1
+
+
 def test_reference_arm_on_other_ranks_does_nothing():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2",
