@@ -410,34 +410,32 @@ def e1_stats(x: np.ndarray, s: np.ndarray, c: np.ndarray) -> dict:
 
 
 def time_loop(torch, fn, steps: int, warmup: int, dist: Dist, sampler=None):
-    """W untimed steps, then K steps between barriers + synchronizes, with a
-    CUDA event pair per step on the current stream.  Returns (wall-equivalent
-    device ms for all K steps, [per-step ms], clocks)."""
+    """W untimed steps, then K steps back to back between barriers +
+    synchronizes, with one CUDA event before the first and one after the last
+    on the current stream (nothing else is enqueued between steps, so
+    consecutive launches can overlap one's drain with the next one's start,
+    as in any stream of calls).  Returns (device ms for all K steps, mean ms
+    per step, clocks)."""
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(steps)]
     t_begin = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     w0 = time.time()
     t_begin.record(stream)
-    for a, b in ev:
-        a.record(stream)
+    for _ in range(steps):
         fn()
-        b.record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
     w1 = time.time()
     dist.barrier()
     torch.cuda.synchronize()
     total = t_begin.elapsed_time(t_end)
-    per = [a.elapsed_time(b) for a, b in ev]
     clocks = sampler.summary(w0, w1) if sampler else None
-    return total, per, clocks
+    return total, total / steps, clocks
 
 
 # -----------------------------------------------------------------------------
@@ -538,8 +536,7 @@ def cuda_libm_context(torch, x_np, x, s, c, dist, steps: int) -> dict:
             st = torch.cuda.current_stream().cuda_stream
             run = lambda: lib.context_libm_sincos(x.data_ptr(), s.data_ptr(), c.data_ptr(), n,
                                                   fast, st)
-            total, per, _ = time_loop(torch, run, steps, 3, dist)
-            ms = statistics.mean(per)
+            total, ms, _ = time_loop(torch, run, steps, 3, dist)
             err = fp64_errors(x_np[idx], s[it].cpu().numpy().astype(np.float64),
                               c[it].cpu().numpy().astype(np.float64))
             key = name if variant == "default" else f"{name} [{variant}]"
@@ -596,10 +593,9 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         c = torch.empty_like(s)
         if autotune:
             api.sincos_autotune_pairs(xt, s, c, red, coef)
-        total, per, _ = time_loop(torch, lambda: api.sincos_pairs_ex(xt, s, c, red, coef), k, 3,
+        total, ms, _ = time_loop(torch, lambda: api.sincos_pairs_ex(xt, s, c, red, coef), k, 3,
                                   dist)
         bytes_ = x.size * (4 + 2 * s.element_size())
-        ms = statistics.mean(per)
         err = fp64_errors(x[idx.cpu().numpy()], s[idx].float().cpu().numpy().astype(np.float64),
                           c[idx].float().cpu().numpy().astype(np.float64))
         prec[name] = {"pairs_per_s": x.size / (ms * 1e-3), "gbs": bytes_ / (ms * 1e-3) / 1e9,
@@ -612,8 +608,7 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     z = torch.empty(x.size, dtype=torch.complex64, device="cuda")
     if autotune:
         api.sincos_autotune_expi(xt, z)
-    total, per, _ = time_loop(torch, lambda: api.sincos_expi(xt, z), k, 3, dist)
-    ms = statistics.mean(per)
+    total, ms, _ = time_loop(torch, lambda: api.sincos_expi(xt, z), k, 3, dist)
     zs = torch.view_as_real(z[idx]).cpu().numpy().astype(np.float64)
     out["expi_complex64_2p26"] = {"gbs": 12 * x.size / (ms * 1e-3) / 1e9, "ms": ms,
                                   "frac_of_peak": 12 * x.size / (ms * 1e-3) / 1e9 / peak,
@@ -634,12 +629,11 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     sampler = ClockSampler(gpu_query_id(torch)) if dist.rank == 0 else None
     time.sleep(0.3 if sampler else 0)
     t0 = time.time()
-    total, per, _ = time_loop(torch, lambda: api.sincos_huygens(P, Q, A, w.k, u),
+    total, ms, _ = time_loop(torch, lambda: api.sincos_huygens(P, Q, A, w.k, u),
                               max(20, k // 4), 3, dist)
     clocks = sampler.summary(t0, time.time()) if sampler else None
     if sampler:
         sampler.stop()
-    ms = statistics.mean(per)
     terms = m * nsrc
     u_np = torch.view_as_real(u).cpu().numpy()
     hy_err = huygens_fp64_errors(w, u_np, np.random.default_rng(0).choice(m, 256, replace=False))
@@ -669,8 +663,7 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     gx = torch.empty_like(xt)
     if autotune:
         api.sincos_autotune_backward(gs, gc, s, c, gx)
-    total, per, _ = time_loop(torch, lambda: api.sincos_backward(gs, gc, s, c, gx), k, 3, dist)
-    ms = statistics.mean(per)
+    total, ms, _ = time_loop(torch, lambda: api.sincos_backward(gs, gc, s, c, gx), k, 3, dist)
     bwd = {"gbs": 20 * xt.numel() / (ms * 1e-3) / 1e9, "ms": ms,
            "plan": api.sincos_plan_get("backward", "f32", xt.numel())}
     bwd["frac_of_peak"] = bwd["gbs"] / peak
@@ -686,8 +679,8 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         ss, cc = api.sincos_autograd(xg)
         torch.autograd.backward([ss, cc], [gs, gc])
         xg.grad = None
-    total, per, _ = time_loop(torch, fwd_bwd, max(10, k // 4), 3, dist)
-    bwd["autograd_fwd_bwd_ms"] = statistics.mean(per)
+    total, ms, _ = time_loop(torch, fwd_bwd, max(10, k // 4), 3, dist)
+    bwd["autograd_fwd_bwd_ms"] = ms
     out["differentiation_2p26"] = bwd
     del xt, gs, gc, s, c, gx, xg
 
@@ -703,11 +696,11 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     if autotune:
         api.sincos_autotune_batched(segs, lens)
     bat["plan"] = api.sincos_plan_get("batched", "f32", b.count)
-    total, per, _ = time_loop(torch, lambda: api.sincos_batched(segs, lens), k, 3, dist)
-    bat["persistent_gbs"] = bytes_ / (statistics.mean(per) * 1e-3) / 1e9
+    total, ms, _ = time_loop(torch, lambda: api.sincos_batched(segs, lens), k, 3, dist)
+    bat["persistent_gbs"] = bytes_ / (ms * 1e-3) / 1e9
     g = api.BatchedGraph(segs, lens)
-    total, per, _ = time_loop(torch, g.launch, k, 3, dist)
-    bat["graph_gbs"] = bytes_ / (statistics.mean(per) * 1e-3) / 1e9
+    total, ms, _ = time_loop(torch, g.launch, k, 3, dist)
+    bat["graph_gbs"] = bytes_ / (ms * 1e-3) / 1e9
     bat["graph_frac_of_peak"] = bat["graph_gbs"] / peak
     g.close()
     offs = b.offsets.tolist()
@@ -717,8 +710,8 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     def separate():
         for v in views:
             api.sincos_pairs(*v)
-    total, per, _ = time_loop(torch, separate, 5, 1, dist)
-    bat["separate_launches_gbs"] = bytes_ / (statistics.mean(per) * 1e-3) / 1e9
+    total, ms, _ = time_loop(torch, separate, 5, 1, dist)
+    bat["separate_launches_gbs"] = bytes_ / (ms * 1e-3) / 1e9
     graph = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream()
     cap.wait_stream(torch.cuda.current_stream())
@@ -728,8 +721,8 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         with torch.cuda.graph(graph, stream=cap):
             separate()
     torch.cuda.synchronize()
-    total, per, _ = time_loop(torch, graph.replay, 10, 2, dist)
-    bat["separate_launches_graph_gbs"] = bytes_ / (statistics.mean(per) * 1e-3) / 1e9
+    total, ms, _ = time_loop(torch, graph.replay, 10, 2, dist)
+    bat["separate_launches_graph_gbs"] = bytes_ / (ms * 1e-3) / 1e9
     del graph
     bi = batch_sample(b.offsets, b.lens)
     bit = torch.from_numpy(bi).cuda()
@@ -768,8 +761,8 @@ def run_ours(args, dist: Dist):
     sampler = ClockSampler(gpu_query_id(torch)) if dist.rank == 0 else None
     time.sleep(0.3 if sampler else 0)
     launches0 = api.sincos_launch_count()
-    total_ms, per, clocks = time_loop(torch, lambda: api.sincos_pairs(x, s, c), args.steps,
-                                      args.warmup, dist, sampler)
+    total_ms, kernel_ms, clocks = time_loop(torch, lambda: api.sincos_pairs(x, s, c), args.steps,
+                                            args.warmup, dist, sampler)
     launches = api.sincos_launch_count() - launches0 - args.warmup
     # re-measure once if the clocks show a thermal or hardware slowdown
     bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
@@ -777,8 +770,8 @@ def run_ours(args, dist: Dist):
     if clocks and bad & set(clocks.get("reasons", [])):
         remeasured = True
         launches0 = api.sincos_launch_count()
-        total_ms, per, clocks = time_loop(torch, lambda: api.sincos_pairs(x, s, c), args.steps,
-                                          args.warmup, dist, sampler)
+        total_ms, kernel_ms, clocks = time_loop(torch, lambda: api.sincos_pairs(x, s, c),
+                                                args.steps, args.warmup, dist, sampler)
         launches = api.sincos_launch_count() - launches0 - args.warmup
     if sampler:
         sampler.stop()
@@ -789,7 +782,6 @@ def run_ours(args, dist: Dist):
     # whole-job pairs/s: the slowest rank's time bounds the job
     value = (n_total * args.steps / (max_ms * 1e-3) if args.split
              else aggregate_value(dist.world, n, args.steps, max_ms))
-    kernel_ms = statistics.mean(per)
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_PAIR * n / (kernel_ms * 1e-3) / 1e9
     traffic = profiled_traffic()
@@ -810,7 +802,7 @@ def run_ours(args, dist: Dist):
         ws = torch.empty(api.sincos_host_workspace_bytes("f32", 1 << 24), dtype=torch.uint8,
                          device="cuda")
         e_steps = max(3, min(args.steps, 10))
-        tot, per_e, _ = time_loop(torch, lambda: api.sincos_pairs_host(xh, sh, ch, ws), e_steps,
+        tot, _, _ = time_loop(torch, lambda: api.sincos_pairs_host(xh, sh, ch, ws), e_steps,
                                   2, dist)
         tot = dist.max(tot)
         route = api.sincos_host_last_path()

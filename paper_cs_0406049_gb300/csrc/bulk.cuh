@@ -85,6 +85,44 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return false;
 }
 
+// Programmatic dependent launch.  A bulk kernel is launched with
+// programmatic stream serialization (launch_bulk_pdl), so it may start while
+// the previous kernel on the stream is still draining.  It lets the kernel
+// after it start as early (pdl_release at its own start: that kernel cannot
+// fit on an SM before this one's CTA there has exited, and it waits in turn),
+// and sets up its shared memory and barriers before pdl_acquire, which blocks
+// until every earlier kernel on the stream has completed and its memory
+// writes are visible.  No global memory is touched before pdl_acquire, so the
+// results are those of plain stream order.  Without the launch attribute both
+// are no-ops.
+__device__ __forceinline__ void pdl_release()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+__device__ __forceinline__ void pdl_acquire()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launch `kernel` with programmatic stream serialization (see pdl_release).
+template <class... KArgs, class... Args>
+static cudaError_t launch_bulk_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                   cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes,
                                           uint32_t bar)
 {
@@ -173,6 +211,7 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
     __shared__ int64_t issued[kBulkStages];
     __shared__ int give_up;
 
+    pdl_release();
     const float *xg = x + head;
     OutT *sg = s + head;
     OutT *cg = c + head;
@@ -187,6 +226,7 @@ k_forward_bulk(const float *x, OutT *s, OutT *c, int64_t n, int64_t head, int64_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    pdl_acquire();
     if (tid == 0) {
         for (int st = 0; st < kBulkStages; ++st) {
             const int64_t ch = blockIdx.x + (int64_t)st * gridDim.x;
@@ -277,8 +317,10 @@ static int launch_forward_bulk_nt(const float *x, OutT *s, OutT *c, int64_t n, i
     const int64_t nchunks = (n - head) / CH;
     int64_t grid = (int64_t)per_sm * dev.sms;
     if (nchunks < grid) grid = nchunks > 0 ? nchunks : 1;
-    k_forward_bulk<OutT, RED, COEF, NT, CH><<<(unsigned)grid, NT, smem, st>>>(x, s, c, n, head,
-                                                                              nchunks);
+    const cudaError_t e = launch_bulk_pdl(k_forward_bulk<OutT, RED, COEF, NT, CH>,
+                                          dim3((unsigned)grid), dim3(NT), smem, st, x, s, c, n,
+                                          head, nchunks);
+    if (e != cudaSuccess) return cuda_fail(e, "bulk forward kernel launch");
     return check_launch("bulk forward kernel launch");
 }
 

@@ -94,6 +94,7 @@ k_expi_bulk(const float *x, float *z, int64_t n, int64_t head, int64_t nchunks)
     __shared__ int64_t issued[kBulkStages];
     __shared__ int give_up;
 
+    pdl_release();
     const float *xg = x + head;
     float *zg = z + 2 * head;
     const int tid = threadIdx.x;
@@ -107,6 +108,7 @@ k_expi_bulk(const float *x, float *z, int64_t n, int64_t head, int64_t nchunks)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    pdl_acquire();                 // no global access before the previous kernel is done
     if (tid == 0) {
         for (int st = 0; st < kBulkStages; ++st) {
             const int64_t ch = blockIdx.x + (int64_t)st * gridDim.x;
@@ -225,7 +227,9 @@ static int launch_expi_bulk(const float *x, float *z, int64_t n, int64_t head,
     const int64_t nchunks = (n - head) / kBulkChunk;
     int64_t grid = (int64_t)per_sm * dev.sms;
     if (nchunks < grid) grid = nchunks > 0 ? nchunks : 1;
-    k_expi_bulk<RED, COEF, NT><<<(unsigned)grid, NT, smem, st>>>(x, z, n, head, nchunks);
+    const cudaError_t e = launch_bulk_pdl(k_expi_bulk<RED, COEF, NT>, dim3((unsigned)grid),
+                                          dim3(NT), smem, st, x, z, n, head, nchunks);
+    if (e != cudaSuccess) return cuda_fail(e, "exp(ix) bulk kernel launch");
     return check_launch("expi bulk kernel launch");
 }
 
