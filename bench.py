@@ -44,6 +44,12 @@ BYTES_PER_PAIR = 12            # 4 B angle read + 4 B sine + 4 B cosine written
 # 26 for the pair with the compensated reduction, 4 for the complex product
 # and 2 accumulating FMAs.
 HUYGENS_OPS_PER_TERM = 41
+# FMA-pipe operations per term of the bit-exact kernel at the least: the 39
+# operations of the definition other than the square root and the reciprocal,
+# plus the 9 FMA-pipe operations of the correctly rounded root and reciprocal
+# (7 and 2 Newton steps after rsqrt.approx and rcp.approx, which run on the
+# XU pipe).  At one operation per FP32 lane per clock this bounds the kernel.
+HUYGENS_FMA_OPS_BIT_EXACT = 48
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0      # only when the measured-peaks file is absent
 E2E_ROUTES = {
@@ -647,7 +653,11 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu,
                      "unit": "TFLOP32-ops/s", "frac": achieved / peak_alu,
                      "peak_kind": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz} MHz",
-                     "ops_per_term": HUYGENS_OPS_PER_TERM},
+                     "ops_per_term": HUYGENS_OPS_PER_TERM,
+                     "fma_pipe_ops_per_term_bit_exact": HUYGENS_FMA_OPS_BIT_EXACT,
+                     "ceiling_bit_exact_terms_per_s": peak_alu * 1e12 / HUYGENS_FMA_OPS_BIT_EXACT,
+                     "frac_of_bit_exact_ceiling": terms / (ms * 1e-3) /
+                                                  (peak_alu * 1e12 / HUYGENS_FMA_OPS_BIT_EXACT)},
         "errors": hy_err,
         "clocks": clocks}
     del P, Q, A, u

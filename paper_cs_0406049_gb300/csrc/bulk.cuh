@@ -28,10 +28,14 @@ constexpr int kBulkChunk = 8192;   // angles per stage (32 KB)
 constexpr int kBulkStages = 2;
 // A bounded wait gives up after this much wall-clock time (%globaltimer), far
 // beyond any healthy stage (a 32 KB copy takes microseconds), so a slow but
-// healthy copy on a busy GPU cannot trip it.  The poll count is capped too,
-// far beyond the time limit (each poll suspends in try_wait), so the loop
-// ends even if the timer were not to advance.
+// healthy copy on a busy GPU cannot trip it.  The clock is read once every
+// kBulkWaitClockEvery polls only: a healthy wait ends long before the first
+// read, and the polling loop stays as tight as a plain count (reading a clock
+// after the first failed poll cost the batched ring kernel 2 % in an A/B).
+// The poll count is capped too, far beyond the time limit, so the loop ends
+// even if the timer were not to advance.
 constexpr unsigned long long kBulkWaitNs = 1000000000ull;   // 1 s
+constexpr unsigned kBulkWaitClockEvery = 1024;
 constexpr unsigned kBulkWaitPollCap = 1u << 28;
 
 // Per translation unit; each TU that launches bulk kernels reports its own.
@@ -70,17 +74,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return done != 0;
 }
 
-// Wait for phase `parity` of the barrier for at most limit_ns of wall-clock
-// time; false if it gave up.  The clock is read only once the first test
-// has failed.
+// Wait for phase `parity` of the barrier for at most about limit_ns of
+// wall-clock time (measured from the first clock read, kBulkWaitClockEvery
+// polls in); false if it gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                                                   unsigned long long limit_ns = kBulkWaitNs)
 {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 0; it < kBulkWaitPollCap; ++it) {
+    unsigned long long t0 = 0;
+    for (unsigned it = 1; it <= kBulkWaitPollCap; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 >= limit_ns) return false;
+        if (it % kBulkWaitClockEvery == 0) {
+            const unsigned long long t = global_ns();
+            if (it == kBulkWaitClockEvery) t0 = t;
+            else if (t - t0 >= limit_ns) return false;
+        }
     }
     return false;
 }

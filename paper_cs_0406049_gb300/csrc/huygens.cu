@@ -23,7 +23,7 @@
 //       scalar.  About 47 instructions per term; each packed instruction
 //       holds the FMA pipe for two cycles, so that pipe is the bound.
 // Pairing points instead of sources halves the warps and loses to latency.
-#include "core_x2.cuh"
+#include "core_rt.cuh"
 #include "trace.h"
 #include "internal.h"
 
@@ -66,9 +66,8 @@ __global__ void k_huygens(const float *px, const float *py, const float *pz, int
                 const float dx = __fsub_rn(x[p], q.x);
                 const float dy = __fsub_rn(y[p], q.y);
                 const float dz = __fsub_rn(z[p], q.z);
-                const float r =
-                    __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
-                const float w = __frcp_rn(r);
+                float r, w;
+                root_recip(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))), r, w);
                 float s, c;
                 pair<RED, COEF_NORMALIZED>(__fmul_rn(k, r), s, c);
                 const float pr = __fmaf_rn(q.w, c, -__fmul_rn(aim, s));
@@ -146,8 +145,8 @@ __global__ void __launch_bounds__(1024, P == 1 ? 2 : 1) k_huygens_x2(const float
                 const float2 dy = __fadd2_rn(y[p], nqy);
                 const float2 dz = __fadd2_rn(z[p], nqz);
                 const float2 rr = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-                const float2 r = make_float2(__fsqrt_rn(rr.x), __fsqrt_rn(rr.y));
-                const float2 w = make_float2(__frcp_rn(r.x), __frcp_rn(r.y));
+                float2 r, w;
+                root_recip_x2(rr, r, w);
                 float2 sv, cv;
                 pair_x2<RED, COEF_NORMALIZED>(__fmul2_rn(k2, r), sv, cv);
                 const float2 pr = __ffma2_rn(are, cv, __fmul2_rn(naim, sv));
@@ -163,9 +162,8 @@ __global__ void __launch_bounds__(1024, P == 1 ? 2 : 1) k_huygens_x2(const float
                 const float dx = __fadd_rn(x[p].x, f[0]);
                 const float dy = __fadd_rn(y[p].x, f[2]);
                 const float dz = __fadd_rn(z[p].x, f[4]);
-                const float r =
-                    __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
-                const float w = __frcp_rn(r);
+                float r, w;
+                root_recip(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))), r, w);
                 float sv, cv;
                 pair<RED, COEF_NORMALIZED>(__fmul_rn(k, r), sv, cv);
                 ure[p] = __fmaf_rn(w, __fmaf_rn(f[6], cv, __fmul_rn(f[10], sv)), ure[p]);

@@ -229,12 +229,14 @@ bool stream_is_capturing(cudaStream_t st)
 // often a lucky one, so the few fastest are then timed again round-robin --
 // one burst of back-to-back runs of each per pass, so that a change of clock
 // or of L2 state shifts them all alike, and so that what is timed is the
-// steady rate of repeated calls, launch gaps included -- and the lowest
+// steady rate of repeated calls, launch gaps included (and the overlap that
+// programmatic dependent launch gives the bulk kernels: 8 runs per burst, so
+// that 7 of them can follow their predecessor directly) -- and the lowest
 // median of those passes wins.
 constexpr int kScreenReps = 3;
 constexpr int kFinalists = 6;
 constexpr int kConfirmPasses = 9;
-constexpr int kConfirmBurst = 4;
+constexpr int kConfirmBurst = 8;
 
 template <class F>
 int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F &&launch_with,
