@@ -502,8 +502,9 @@ def cpu_baseline(x: np.ndarray) -> dict:
     xs = x[: 1 << 26]
     s = np.empty_like(xs)
     c = np.empty_like(xs)
+    # about 20 s of CPU work: 1.5 s of wall time on 16 cores, or 20 passes
     reps, used, t0 = 0, 0, time.perf_counter()
-    while reps < 2 or (time.perf_counter() - t0 < 3.0 and reps < 20):
+    while reps < 2 or (time.perf_counter() - t0 < 20.0 / cores and reps < 200) or reps < 20:
         used = oracle.sincos_mt(xs, s, c, threads=cores)
         reps += 1
     dt = time.perf_counter() - t0
