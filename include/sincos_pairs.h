@@ -351,8 +351,8 @@ int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan);
 
 /* Time every candidate plan on the caller's own buffers (writes s and c; x
  * must not alias them), store the fastest for this (op, dtype, n bucket) and
- * return it in *best.  Timing: every candidate as the median of three single
- * launches, then the six fastest round-robin over nine passes of eight
+ * return it in *best.  Timing: every candidate as the median of three bursts
+ * of two launches, then the six fastest round-robin over nine passes of eight
  * back-to-back launches each; the lowest median wins.  Synchronizes
  * `stream`.  Must not be called while `stream` is captured. */
 int sincos_autotune_pairs(const float *x, void *s, void *c, int64_t n, int out_dtype,

@@ -33,6 +33,12 @@ int cuda_fail(cudaError_t e, const char *what)
     return SINCOS_ECUDA;
 }
 
+int fail_with(int status, const char *what)
+{
+    g_last_error = what;
+    return status;
+}
+
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 int check_launch(const char *what)

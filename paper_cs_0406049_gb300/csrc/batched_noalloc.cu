@@ -81,7 +81,10 @@ extern "C" int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *len
     if (count == 0) return SINCOS_OK;
     if (!segs || !lens) return SINCOS_EINVAL;
     if (!aligned_to(segs, 8) || !aligned_to(lens, 8)) return SINCOS_EINVAL;
-    if (count > SINCOS_NOALLOC_MAX_SEGMENTS) return SINCOS_EUNSUPPORTED;
+    if (count > SINCOS_NOALLOC_MAX_SEGMENTS)
+        return fail_with(SINCOS_EUNSUPPORTED,
+                         "sincos_batched_noalloc: count exceeds SINCOS_NOALLOC_MAX_SEGMENTS "
+                         "(65536 arrays), the size of the library's fixed scratch array");
     const DeviceInfo *dev = nullptr;
     int rc = current_device(&dev);
     if (rc != SINCOS_OK) return rc;

@@ -444,6 +444,11 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
     __shared__ int64_t wa[32], wb[32];
     __shared__ int64_t red[kRunBatch][32], tot[kRunBatch], ctot[kRunChunks];
 
+    // Programmatic dependent launch (see pdl_release): the descriptors and
+    // lengths may come from the previous kernel on the stream, so every
+    // global access waits for it.
+    pdl_release();
+    pdl_acquire();
     ring_run<OutT>(segs, lens, count, &run, wa, wb, red, tot, ctot);
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -622,8 +627,17 @@ static int launch_batched_ring(const sincos_seg *segs, const int64_t *lens, int 
     const int grid = batched_grid(per_sm, dev);
     (void)sched;                      // the ring kernel schedules itself
     void *args[] = {(void *)&segs, (void *)&lens, (void *)&count};
-    const cudaError_t e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3((unsigned)(block + 32)),
-                                           args, smem, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)(block + 32));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     if (e != cudaSuccess) return cuda_fail(e, "batched ring kernel launch");
     return check_launch("batched ring kernel launch");
 }

@@ -26,6 +26,9 @@ int current_device(const DeviceInfo **info);
 
 // Record a failed CUDA call for sincos_last_error(); returns SINCOS_ECUDA.
 int cuda_fail(cudaError_t e, const char *what);
+// Record `what` for sincos_last_error() and return `status` (errors that are
+// not CUDA failures but need more words than the status code).
+int fail_with(int status, const char *what);
 // cudaGetLastError() after a launch, mapped to a status.
 int check_launch(const char *what);
 // Count `k` kernel launches (sincos_launch_count()).

@@ -225,7 +225,9 @@ bool stream_is_capturing(cudaStream_t st)
 }
 
 // Two rounds.  The screen times every candidate (one warm-up run, median of
-// three single runs); with a hundred candidates the single fastest median is
+// three bursts of two back-to-back runs, so that a plan whose launches
+// overlap is not screened out on isolated launches); with a hundred
+// candidates the single fastest median is
 // often a lucky one, so the few fastest are then timed again round-robin --
 // one burst of back-to-back runs of each per pass, so that a change of clock
 // or of L2 state shifts them all alike, and so that what is timed is the
@@ -234,6 +236,7 @@ bool stream_is_capturing(cudaStream_t st)
 // that 7 of them can follow their predecessor directly) -- and the lowest
 // median of those passes wins.
 constexpr int kScreenReps = 3;
+constexpr int kScreenBurst = 2;
 constexpr int kFinalists = 6;
 constexpr int kConfirmPasses = 9;
 constexpr int kConfirmBurst = 8;
@@ -251,7 +254,7 @@ int tune(const DeviceInfo &dev, int op, int dtype, int64_t n, cudaStream_t st, F
         if (run() != SINCOS_OK) continue;
         std::vector<float> ms;
         for (int r = 0; r < kScreenReps; ++r) {
-            const float t = timer.once(run, st);
+            const float t = timer.once(run, st, kScreenBurst);
             if (t < 0.f) break;
             ms.push_back(t);
         }

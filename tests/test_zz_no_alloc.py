@@ -6,7 +6,7 @@ cannot afford the device synchronization cudaMalloc may cause, code with a
 memory budget fixed at start-up.  Its schedule scratch is a fixed array inside
 the library, which only register plans (vec_bytes 16 or 32) use: the ring
 kernel of the binary32 default plan schedules itself.  So most checks here run
-under register plans (forced for binary32, the defaults for 16-bit outputs),
+under register plans (forced; the defaults for 16-bit outputs are such plans),
 where the launch counter moves by two per call (schedule kernel + tile
 kernel), which shows the scratch array was written and read.
 
@@ -103,12 +103,11 @@ def test_noalloc_register_plans_two_calls(cuda_lib, plan):
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_noalloc_16bit_default_plans_two_calls(cuda_lib, dtype):
-    """16-bit outputs on their default plans, which are register plans."""
-    for count in (3000, 41):
-        plan = api.sincos_plan_get("batched", dtype, count)
-        assert plan["vec_bytes"] in (16, 32), plan
-    _two_calls(cuda_lib, dtype=dtype, red="compensated", kernels=2)
+def test_noalloc_16bit_register_plans_two_calls(cuda_lib, dtype):
+    """16-bit outputs under register plans (their defaults; forced here so
+    that a plan tuned earlier in the same process cannot change the path)."""
+    with forced_plan("batched", dtype, REGISTER_PLANS["reg32"]):
+        _two_calls(cuda_lib, dtype=dtype, red="compensated", kernels=2)
 
 
 def test_noalloc_dagger_register_plan(cuda_lib):
@@ -132,6 +131,7 @@ def test_noalloc_limits(cuda_lib):
     assert lib.sincos_batched_noalloc(segs.data_ptr(), lens.data_ptr(), n, _lib.F32,
                                       _lib.RED_PLAIN, _lib.COEF_NORMALIZED,
                                       stream) == _lib.EUNSUPPORTED
+    assert b"SINCOS_NOALLOC_MAX_SEGMENTS" in lib.sincos_last_error()
     assert lib.sincos_batched_noalloc(None, None, 0, _lib.F32, _lib.RED_PLAIN,
                                       _lib.COEF_NORMALIZED, stream) == _lib.OK
     assert lib.sincos_launch_count() == before
