@@ -172,3 +172,59 @@ def test_cpulist_parsing():
     assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
     assert bench.parse_cpulist("5") == {5}
     assert bench.parse_cpulist("") == set()
+
+
+def test_error_helpers_on_rounded_exact_values():
+    """The bench's FP64 error statements: correctly rounded binary32 values
+    of the exact results come out within half an ulp (and a planted error
+    of one ulp of 1.0 comes out as one)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-50, 50, 1 << 16).astype(np.float32)
+    xd = x.astype(np.float64)
+    s = np.sin(xd).astype(np.float32).astype(np.float64)
+    c = np.cos(xd).astype(np.float32).astype(np.float64)
+    e = bench.fp64_errors(x, s, c)
+    assert e["max_abs"] <= 2.0 ** -25 and e["max_abs_ulp1"] <= 0.5
+    assert e["max_ulp_rel_ge_2m4"] <= 0.5 + 1e-9 and e["sample"] == x.size
+    s_bad = s.copy()
+    s_bad[7] += 2.0 ** -23
+    assert bench.fp64_errors(x, s_bad, c)["max_abs_ulp1"] >= 0.75   # 1 ulp(1) less a rounding
+    gs = rng.standard_normal(x.size).astype(np.float32)
+    gc = rng.standard_normal(x.size).astype(np.float32)
+    gx = (gs.astype(np.float64) * np.cos(xd) - gc.astype(np.float64) * np.sin(xd)).astype(np.float32)
+    b = bench.backward_fp64_errors(x, gs, gc, gx)
+    assert b["max_rel_to_abs_gs_plus_abs_gc"] <= 2.0 ** -24
+
+
+def test_huygens_error_helper_and_batch_sample():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+
+    class W:
+        pass
+    rng = np.random.default_rng(6)
+    w = W()
+    w.p = tuple(rng.uniform(-5, 5, 40).astype(np.float32) for _ in range(2)) + \
+        (np.full(40, 30.0, np.float32),)
+    w.q = tuple(rng.uniform(-2, 2, 25).astype(np.float32) for _ in range(3))
+    w.a = (rng.standard_normal(25) + 1j * rng.standard_normal(25)).astype(np.complex64)
+    w.k = float(np.float32(2 * np.pi))
+    p = [v.astype(np.float64) for v in w.p]
+    q = [v.astype(np.float64) for v in w.q]
+    r = np.sqrt(sum((p[d][:, None] - q[d][None, :]) ** 2 for d in range(3)))
+    exact = (w.a.astype(np.complex128)[None, :] * np.exp(1j * w.k * r) / r).sum(axis=1)
+    u = np.stack([exact.real, exact.imag], axis=1).astype(np.float32)
+    pts = np.arange(0, 40, 3)
+    h = bench.huygens_fp64_errors(w, u, pts)
+    assert h["sample"] == pts.size and h["max_rel_to_sum_abs_terms"] <= 2.0 ** -23
+    offs, lens = np.array([0, 10, 500, 501]), np.array([10, 490, 1, 300])
+    idx = bench.batch_sample(offs, lens)
+    assert np.all(np.diff(idx) > 0) and idx.min() == 0 and idx.max() == 800
+    for o, n in zip(offs, lens):
+        k = min(n, 64)
+        assert np.isin(np.arange(o, o + k), idx).all()
+        assert np.isin(np.arange(o + n - k, o + n), idx).all()
