@@ -52,6 +52,15 @@ HUYGENS_OPS_PER_TERM = 41
 HUYGENS_FMA_OPS_BIT_EXACT = 48
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0      # only when the measured-peaks file is absent
+# The paper's own figures (Sec. Results), quoted for context: other hardware,
+# one core, not a target.
+PAPER_CONTEXT = {
+    "hardware": "PowerPC 7400 (G4), 500 MHz, AltiVec 4-wide, one core",
+    "latency_ns_per_4_pairs": 140,
+    "interleaved_pairs_per_s": 8.0e7,
+    "accuracy_normalized": {"rms_euclid": 1.2e-7, "max_euclid": 4.8e-7, "max_amplitude": 1.8e-7},
+    "accuracy_dagger": {"rms_euclid": 9.8e-8, "max_euclid": 3.8e-7},
+}
 E2E_ROUTES = {
     "zero-copy": "sincos_pairs_host on page-locked, mapped host buffers: one kernel reads x "
                  "and writes s, c across NVLink-C2C",
@@ -871,6 +880,7 @@ def run_ours(args, dist: Dist):
                          "bytes_per_launch": BYTES_PER_PAIR * n, "kernel_ms": kernel_ms,
                          **vendor_peak(torch, achieved)},
             "errors_vs_fp64": err,
+            "paper_context": PAPER_CONTEXT,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
