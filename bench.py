@@ -567,6 +567,10 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     out = {}
     k = max(20, min(steps_hint, 200))
     peak, _ = measured_peak()
+    vendor = vendor_peak(torch, 1.0).get("peak_vendor")   # nominal HBM GB/s, or None
+
+    def of_vendor(gbs):
+        return gbs / vendor if vendor else None
 
     # plain: 2^20 angles U[-pi, pi) (12.6 MB, L2-resident), L2 flushed before
     # every call (the flush also keeps the host ahead of the GPU, so the event
@@ -615,7 +619,9 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         err = fp64_errors(x[idx.cpu().numpy()], s[idx].float().cpu().numpy().astype(np.float64),
                           c[idx].float().cpu().numpy().astype(np.float64))
         prec[name] = {"pairs_per_s": x.size / (ms * 1e-3), "gbs": bytes_ / (ms * 1e-3) / 1e9,
-                      "frac_of_peak": bytes_ / (ms * 1e-3) / 1e9 / peak, "ms": ms, "errors": err,
+                      "frac_of_peak": bytes_ / (ms * 1e-3) / 1e9 / peak,
+                      "frac_of_vendor_peak": of_vendor(bytes_ / (ms * 1e-3) / 1e9),
+                      "ms": ms, "errors": err,
                       "plan": api.sincos_plan_get("pairs", dt, x.size)}
         del s, c
     out["precision_2p26"] = prec
@@ -628,6 +634,7 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     zs = torch.view_as_real(z[idx]).cpu().numpy().astype(np.float64)
     out["expi_complex64_2p26"] = {"gbs": 12 * x.size / (ms * 1e-3) / 1e9, "ms": ms,
                                   "frac_of_peak": 12 * x.size / (ms * 1e-3) / 1e9 / peak,
+                                  "frac_of_vendor_peak": of_vendor(12 * x.size / (ms * 1e-3) / 1e9),
                                   "reduction": "plain",
                                   "errors": fp64_errors(x[idx.cpu().numpy()], zs[:, 1], zs[:, 0]),
                                   "plan": api.sincos_plan_get("expi", "f32", x.size)}
@@ -687,6 +694,7 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     bwd = {"gbs": 20 * xt.numel() / (ms * 1e-3) / 1e9, "ms": ms,
            "plan": api.sincos_plan_get("backward", "f32", xt.numel())}
     bwd["frac_of_peak"] = bwd["gbs"] / peak
+    bwd["frac_of_vendor_peak"] = of_vendor(bwd["gbs"])
     di = np.random.default_rng(0).integers(0, w.x.size, 1 << 20)
     dit = torch.from_numpy(di).cuda()
     bwd["errors"] = {
@@ -722,6 +730,7 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
     total, ms, _ = time_loop(torch, g.launch, k, 3, dist)
     bat["graph_gbs"] = bytes_ / (ms * 1e-3) / 1e9
     bat["graph_frac_of_peak"] = bat["graph_gbs"] / peak
+    bat["graph_frac_of_vendor_peak"] = of_vendor(bat["graph_gbs"])
     g.close()
     offs = b.offsets.tolist()
     ln = b.lens.tolist()
