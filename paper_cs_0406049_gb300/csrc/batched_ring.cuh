@@ -510,13 +510,17 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
 
         // Middles.  When every middle of the stage is on its segment's grid the
         // output stage mirrors the input stage (same offsets), so the whole
-        // stage is one unrolled loop whatever the number of parts.
+        // stage is one unrolled loop whatever the number of parts.  Binary32
+        // tiles take the packed pair (same bits) with the compensated
+        // reduction only: on the 4096-array workload it gave 6153 against
+        // 6081 GB/s there, and 6270 against 6301 with the plain reduction.
+        constexpr bool kPack = RED == RED_COMPENSATED;
         const int mid = nmid[slot];
         if (nout[slot] == mid) {
 #pragma unroll
             for (int j = 0; j < kRingCap / (NT * E); ++j) {
                 const int e = (j * NT + tid) * E;
-                if (e < mid) bulk_tile_vec<RED, COEF, OutT>(xs, so, co, e);
+                if (e < mid) bulk_tile_vec<RED, COEF, OutT, kPack>(xs, so, co, e);
             }
         } else {
             for (int i = 0; i < n; ++i) {
@@ -525,7 +529,7 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
                 const float *xi = xs + p.in_off;
                 if (p.out_off >= 0) {
                     for (int e = tid * E; e < m; e += NT * E)
-                        bulk_tile_vec<RED, COEF, OutT>(xi, so + p.out_off, co + p.out_off, e);
+                        bulk_tile_vec<RED, COEF, OutT, kPack>(xi, so + p.out_off, co + p.out_off, e);
                 } else {
                     OutT *sd = (OutT *)p.s + p.u0;
                     OutT *cd = (OutT *)p.c + p.u0;

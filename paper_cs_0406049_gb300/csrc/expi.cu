@@ -139,10 +139,27 @@ k_expi_bulk(const float *x, float *z, int64_t n, int64_t head, int64_t nchunks)
             const int e = (j * NT + tid) * 4;
             const float4 v = *reinterpret_cast<const float4 *>(xi + e);
             float s0, s1, s2, s3, c0, c1, c2, c3;
-            pair<RED, COEF>(v.x, s0, c0);
-            pair<RED, COEF>(v.y, s1, c1);
-            pair<RED, COEF>(v.z, s2, c2);
-            pair<RED, COEF>(v.w, s3, c3);
+            // The packed pair (same bits) pays with the compensated reduction
+            // only: 6425 against 6337 GB/s at 2^26 and 6621 against 6533 at
+            // 2^28; with the plain one it measured 0.4 % slower.
+            if constexpr (RED == RED_COMPENSATED && COEF == COEF_NORMALIZED) {
+                float2 sa, ca, sb, cb;
+                pair_x2<RED, COEF>(make_float2(v.x, v.y), sa, ca);
+                pair_x2<RED, COEF>(make_float2(v.z, v.w), sb, cb);
+                s0 = sa.x;
+                s1 = sa.y;
+                c0 = ca.x;
+                c1 = ca.y;
+                s2 = sb.x;
+                s3 = sb.y;
+                c2 = cb.x;
+                c3 = cb.y;
+            } else {
+                pair<RED, COEF>(v.x, s0, c0);
+                pair<RED, COEF>(v.y, s1, c1);
+                pair<RED, COEF>(v.z, s2, c2);
+                pair<RED, COEF>(v.w, s3, c3);
+            }
             *reinterpret_cast<float4 *>(zo + 2 * e) = make_float4(c0, s0, c1, s1);
             *reinterpret_cast<float4 *>(zo + 2 * e + 4) = make_float4(c2, s2, c3, s3);
         }
