@@ -49,14 +49,17 @@ sincos_plan default_plan(int op, int dtype)
     // Fastest plans of a GB300 sweep (2^26..2^28 elements, 4096-array batch).
     // About 1024 resident threads per SM with 2..8 vectors in flight each
     // beat full occupancy: fewer concurrent streams keep DRAM pages open.
-    // The binary32 single-array forward defaults to the bulk (TMA-staged)
-    // path; 16-bit outputs run faster on the 32-byte register path.
+    // The single-array forward defaults to the bulk (TMA-staged) path: 8192-
+    // angle stages for binary32, 4096-angle stages (three CTAs per SM) for
+    // 16-bit outputs, which with programmatic dependent launch beat the
+    // 32-byte register path (6480 against 6350 GB/s at 2^26).  Batched
+    // 16-bit outputs keep the register path.
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
     if (op == SINCOS_OP_EXPI) return sincos_plan{512, 2, 1, 0};
     if (op == SINCOS_OP_HUYGENS) return sincos_plan{256, 1, 8, 32};
     if (op == SINCOS_OP_BATCHED)
         return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
-    return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
+    return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{512, 2, 3, 0};
 }
 
 int load_file(const char *path);
