@@ -215,11 +215,36 @@ def measured_sm_max_mhz() -> float:
         return 2070.0
 
 
+def code_only(src: str) -> str:
+    """C++ source with its comments and blank-line runs removed, so that a
+    change of comments alone does not count as a change of the kernel."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif src[i] == '"':                       # string literal: kept as is
+            j = i + 1
+            while j < n and src[j] != '"':
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(src[i])
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).splitlines()]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_source_sha() -> str:
+    """Hash of the timed kernel's source files, comments left out."""
     h = hashlib.sha1()
     for name in FWD_SOURCES:
-        with open(os.path.join(ROOT, "paper_cs_0406049_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_cs_0406049_gb300", "csrc", name)) as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -170,7 +170,7 @@ __device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *c
     // compensated at 2^28).  For 16-bit outputs the packed form needs more
     // registers than three CTAs of 512 threads can share and loses (6066
     // against 6532 GB/s); the batched ring kernel uses it with the compensated
-// reduction only (+1.2 % there, -0.5 % with the plain one).
+    // reduction only (+1.2 % there, -0.5 % with the plain one).
     if constexpr (PACK && COEF == COEF_NORMALIZED && sizeof(OutT) == 4) {
 #pragma unroll
         for (int i = 0; i < E; i += 2) {

@@ -228,3 +228,14 @@ def test_huygens_error_helper_and_batch_sample():
         k = min(n, 64)
         assert np.isin(np.arange(o, o + k), idx).all()
         assert np.isin(np.arange(o + n - k, o + n), idx).all()
+
+
+def test_kernel_hash_ignores_comments_only():
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) { return x + 1; }  // one\n/* two\n three */\n"
+    b = "// another comment\nint f(int x) { return x + 1; }\n\n"
+    c = "int f(int x) { return x + 2; }\n"
+    assert bench.code_only(a) == bench.code_only(b) != bench.code_only(c)
+    assert bench.code_only('const char *s = "// not a comment";') == 'const char *s = "// not a comment";'
+    assert bench.profiled_traffic() is not None      # the committed capture matches the source
