@@ -75,3 +75,36 @@ def test_exp_ix_after_forward(cuda_lib):
     assert_f32_parity(as_np(s2), ts, "third call s")
     assert_f32_parity(as_np(c2), tc, "third call c")
     assert api.sincos_device_wait_timeouts() == 0
+
+
+def test_dependent_chain_in_a_cuda_graph(cuda_lib):
+    """The read-after-write chain captured into a CUDA graph (the bulk
+    launches become programmatic dependencies of the graph) and replayed
+    twice with new angles copied in between."""
+    x = mixed_angles(N, seed=45)
+    x2 = mixed_angles(N, seed=46)
+    src = torch.from_numpy(x).cuda()
+    bufs = [torch.empty(N, device="cuda") for _ in range(4)]
+    cs = [torch.empty(N, device="cuda") for _ in range(3)]
+    bufs[0].copy_(src)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for i in range(3):                     # warm-up outside the capture
+            api.sincos_pairs(bufs[i], bufs[i + 1], cs[i])
+        side.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            for i in range(3):
+                api.sincos_pairs(bufs[i], bufs[i + 1], cs[i])
+    torch.cuda.synchronize()
+    for angles in (x, x2):
+        bufs[0].copy_(torch.from_numpy(angles))
+        g.replay()
+        torch.cuda.synchronize()
+        want = angles
+        for i in range(3):
+            ws, wc = oracle.sincos(want)
+            assert_f32_parity(as_np(bufs[i + 1]), ws, f"graph chain step {i} s")
+            assert_f32_parity(as_np(cs[i]), wc, f"graph chain step {i} c")
+            want = ws
