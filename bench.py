@@ -868,7 +868,22 @@ def run_ours(args, dist: Dist):
                "path": route,
                "path_note": E2E_ROUTES.get(route, route),
                "host_buffers_pinned": placed}
-        del xh, sh, ch, ws
+        del xh, sh, ch
+        if not args.no_extras:
+            # the same call on ordinary (pageable) host memory, which takes the
+            # chunked copy pipeline: what a caller without page-locked buffers gets
+            xp = torch.from_numpy(x_np)
+            sp, cp = torch.empty(n, dtype=torch.float32), torch.empty(n, dtype=torch.float32)
+            p_steps = 3
+            tp, _, _ = time_loop(torch, lambda: api.sincos_pairs_host(xp, sp, cp, ws), p_steps, 1,
+                                 dist)
+            tp = dist.max(tp)
+            e2e["pageable"] = {"value": (n_total if args.split else dist.world * n) * p_steps /
+                                        (tp * 1e-3),
+                               "unit": UNIT, "ms_per_step": tp / p_steps,
+                               "path": api.sincos_host_last_path()}
+            del xp, sp, cp
+        del ws
 
     ext = None
     if not args.no_extras:
