@@ -66,6 +66,9 @@ E2E_ROUTES = {
                  "and writes s, c across NVLink-C2C",
     "pipeline": "sincos_pairs_host through the chunked copy pipeline: host -> device copy, "
                 "kernel, device -> host copy on three rotating streams",
+    "zero-copy-pageable": "sincos_pairs_host on ordinary pageable host memory: one kernel "
+                          "reads x and writes s, c through the host's page tables across "
+                          "NVLink-C2C",
 }
 FWD_SOURCES = ["core.cuh", "core_x2.cuh", "bulk.cuh", "forward.cuh", "forward_f32.cu"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "ncu_forward_f32_bandwidth_2p28.md")
@@ -870,18 +873,24 @@ def run_ours(args, dist: Dist):
                "host_buffers_pinned": placed}
         del xh, sh, ch
         if not args.no_extras:
-            # the same call on ordinary (pageable) host memory, which takes the
-            # chunked copy pipeline: what a caller without page-locked buffers gets
+            # the same call on ordinary (pageable) host memory: what a caller
+            # without page-locked buffers gets (zero-copy where the device
+            # reaches pageable memory), and the copy pipeline on it for context
             xp = torch.from_numpy(x_np)
             sp, cp = torch.empty(n, dtype=torch.float32), torch.empty(n, dtype=torch.float32)
-            p_steps = 3
-            tp, _, _ = time_loop(torch, lambda: api.sincos_pairs_host(xp, sp, cp, ws), p_steps, 1,
-                                 dist)
-            tp = dist.max(tp)
-            e2e["pageable"] = {"value": (n_total if args.split else dist.world * n) * p_steps /
-                                        (tp * 1e-3),
-                               "unit": UNIT, "ms_per_step": tp / p_steps,
-                               "path": api.sincos_host_last_path()}
+            for key, policy, p_steps in (("pageable", "auto", 5), ("pageable_pipeline", "pipeline", 3)):
+                api.sincos_host_route_set(policy)
+                try:
+                    tp, _, _ = time_loop(torch, lambda: api.sincos_pairs_host(xp, sp, cp, ws),
+                                         p_steps, 1, dist)
+                    route_p = api.sincos_host_last_path()
+                finally:
+                    api.sincos_host_route_set("auto")
+                tp = dist.max(tp)
+                e2e[key] = {"value": (n_total if args.split else dist.world * n) * p_steps /
+                                     (tp * 1e-3),
+                            "unit": UNIT, "ms_per_step": tp / p_steps, "path": route_p}
+            assert torch.equal(sp[:1024], s[:1024].cpu()), "pageable path differs from device path"
             del xp, sp, cp
         del ws
 

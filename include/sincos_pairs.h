@@ -268,15 +268,19 @@ int sincos_batched_graph_destroy(sincos_graph g);
 /* The forward (Sec. Methodology, Fig. 1) on host arrays; the data movement
  * has no paper counterpart.  x_host holds n floats; s_host and c_host hold n
  * elements of out_dtype.
- *   If all three buffers are page-locked and mapped into the device's address
- *   space (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping), one
- *   kernel reads x and writes s and c across the host link itself
- *   (zero-copy), and dev_ws is not used.  x may be s or c exactly (binary32
- *   output); any other overlap returns SINCOS_EOVERLAP.
- *   Otherwise x is copied to the device in chunks, each chunk is computed,
- *   and s and c are copied back, with copies and kernels of different chunks
- *   overlapped on internal streams (pageable memory works, but the driver
- *   stages its copies).
+ *   If the device can reach all three buffers, one kernel reads x and writes
+ *   s and c across the host link itself (zero-copy), and dev_ws is not used.
+ *   It can reach page-locked buffers mapped into its address space
+ *   (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping), and, on a
+ *   device that accesses pageable memory through the host's page tables
+ *   (cudaDevAttrPageableMemoryAccess, as GB300 with Grace), ordinary pageable
+ *   memory too (pages the CPU has not touched yet are placed on first access
+ *   by the system).  x may be s or c exactly (binary32 output); any other
+ *   overlap returns SINCOS_EOVERLAP.
+ *   Otherwise, or under SINCOS_HOST_ROUTE_PIPELINE, x is copied to the device
+ *   in chunks, each chunk is computed, and s and c are copied back, with
+ *   copies and kernels of different chunks overlapped on internal streams
+ *   (pageable memory works, but the driver stages its copies).
  *   dev_ws   caller-owned device workspace of ws_bytes for the chunked path,
  *            used as three rotating chunk buffers; sincos_host_workspace_bytes()
  *            gives the size for a given chunk length.  Must be 256-byte
@@ -291,16 +295,29 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
 size_t sincos_host_workspace_bytes(int out_dtype, int64_t chunk_elems);
 
 /* The route the calling thread's most recent sincos_pairs_host call took:
- * SINCOS_HOST_PATH_ZERO_COPY (one kernel on the mapped host buffers),
+ * SINCOS_HOST_PATH_ZERO_COPY (one kernel on page-locked, mapped buffers),
+ * SINCOS_HOST_PATH_ZERO_COPY_PAGEABLE (one kernel, at least one buffer
+ * pageable memory reached through the host's page tables),
  * SINCOS_HOST_PATH_PIPELINE (chunked copies through dev_ws), or
  * SINCOS_HOST_PATH_NONE (no call yet on this thread, n == 0, or the call
  * returned an error).  Data movement only; the paper has no counterpart. */
 typedef enum {
     SINCOS_HOST_PATH_NONE = 0,
     SINCOS_HOST_PATH_ZERO_COPY = 1,
-    SINCOS_HOST_PATH_PIPELINE = 2
+    SINCOS_HOST_PATH_PIPELINE = 2,
+    SINCOS_HOST_PATH_ZERO_COPY_PAGEABLE = 3
 } sincos_host_path;
 int sincos_host_last_path(void);
+
+/* Which routes sincos_pairs_host may take, for the whole process:
+ * SINCOS_HOST_ROUTE_AUTO (the default: zero-copy whenever the device can
+ * reach all three buffers, else the copy pipeline) or
+ * SINCOS_HOST_ROUTE_PIPELINE (always the copy pipeline through dev_ws, for
+ * callers that want the host buffers touched only by copy engines).  Takes
+ * effect for calls that start after it returns.  SINCOS_EINVAL for another
+ * value. */
+typedef enum { SINCOS_HOST_ROUTE_AUTO = 0, SINCOS_HOST_ROUTE_PIPELINE = 1 } sincos_host_route;
+int sincos_host_route_set(int policy);
 
 /* ------------------------------------------------------------------------ */
 /* Launch plans and the autotuner                                            */

@@ -19,7 +19,8 @@ RED_PLAIN, RED_COMPENSATED = 0, 1
 COEF_NORMALIZED, COEF_DAGGER = 0, 1
 OP_PAIRS, OP_BACKWARD, OP_BATCHED, OP_EXPI, OP_HUYGENS = 0, 1, 2, 3, 4
 NOALLOC_MAX_SEGMENTS = 65536
-HOST_PATH_NONE, HOST_PATH_ZERO_COPY, HOST_PATH_PIPELINE = 0, 1, 2
+HOST_PATH_NONE, HOST_PATH_ZERO_COPY, HOST_PATH_PIPELINE, HOST_PATH_ZERO_COPY_PAGEABLE = 0, 1, 2, 3
+HOST_ROUTE_AUTO, HOST_ROUTE_PIPELINE = 0, 1
 
 
 class sincos_plan(ctypes.Structure):
@@ -56,6 +57,7 @@ SIGNATURES = {
     "sincos_pairs_host": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _SZ, _VP]),
     "sincos_host_workspace_bytes": (_SZ, [_INT, _I64]),
     "sincos_host_last_path": (_INT, []),
+    "sincos_host_route_set": (_INT, [_INT]),
     "sincos_plan_get": (_INT, [_INT, _INT, _I64, _PLANP]),
     "sincos_plan_set": (_INT, [_INT, _INT, _I64, _PLANP]),
     "sincos_autotune_pairs": (_INT, [_VP, _VP, _VP, _I64, _INT, _INT, _INT, _VP, _PLANP]),

@@ -289,14 +289,23 @@ def sincos_pairs_host(x_host: torch.Tensor, s_host: torch.Tensor, c_host: torch.
 
 
 _HOST_PATHS = {_lib.HOST_PATH_NONE: "none", _lib.HOST_PATH_ZERO_COPY: "zero-copy",
-               _lib.HOST_PATH_PIPELINE: "pipeline"}
+               _lib.HOST_PATH_PIPELINE: "pipeline",
+               _lib.HOST_PATH_ZERO_COPY_PAGEABLE: "zero-copy-pageable"}
+_HOST_ROUTES = {"auto": _lib.HOST_ROUTE_AUTO, "pipeline": _lib.HOST_ROUTE_PIPELINE}
 
 
 def sincos_host_last_path() -> str:
     """The route of this thread's last sincos_pairs_host call: "zero-copy"
-    (one kernel on the mapped host buffers), "pipeline" (chunked copies) or
-    "none"."""
+    (one kernel on page-locked host buffers), "zero-copy-pageable" (one kernel,
+    pageable memory through the host's page tables), "pipeline" (chunked
+    copies) or "none"."""
     return _HOST_PATHS[lib().sincos_host_last_path()]
+
+
+def sincos_host_route_set(policy: str) -> None:
+    """"auto" (zero-copy whenever the device can reach the buffers) or
+    "pipeline" (always chunked copies), for the whole process."""
+    check(lib().sincos_host_route_set(_HOST_ROUTES[policy]), "sincos_host_route_set")
 
 
 # -----------------------------------------------------------------------------

@@ -66,6 +66,12 @@ int current_device(const DeviceInfo **info)
         d.major = prop.major;
         d.minor = prop.minor;
         d.max_threads_per_sm = prop.maxThreadsPerMultiProcessor;
+        int pageable = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+            cudaGetLastError();
+            pageable = 0;
+        }
+        d.pageable_access = pageable == 1;
         snprintf(d.name, sizeof d.name, "%s", prop.name);
         g_dev_ready[dev] = true;
     }

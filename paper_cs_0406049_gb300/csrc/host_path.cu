@@ -1,14 +1,21 @@
 // host_path.cu -- the forward on host arrays.
 //
-// Page-locked, mapped buffers (cudaHostAlloc, cudaMallocHost, or
-// cudaHostRegister with mapping) are read and written by the kernel itself
+// Host buffers the kernel can reach are read and written by the kernel itself
 // across the host link (zero-copy), with the register path's plain vector
-// loads and stores.  On GB300's NVLink-C2C that moves 272 GB/s against 262
-// for the copy pipeline, which loses its fill and drain.  Other host memory
-// goes through the pipeline: chunked host -> device copy, kernel, device ->
-// host copy, with consecutive chunks on three rotating internal streams, so
-// that one chunk's upload, another's kernel and a third's download proceed at
-// once.  The device side of the pipeline uses only the caller's workspace.
+// loads and stores: page-locked, mapped buffers (cudaHostAlloc,
+// cudaMallocHost, or cudaHostRegister with mapping) on any device, and
+// ordinary pageable memory on devices that access it through the host's page
+// tables (cudaDevAttrPageableMemoryAccess, as GB300 with Grace over
+// NVLink-C2C).  There that moves 272 GB/s for either kind of memory, against
+// 262 for the copy pipeline with page-locked buffers (it loses its fill and
+// drain) and 28 for the pipeline with pageable ones (the driver stages those
+// copies).  Otherwise, or when the caller asks for it
+// (sincos_host_route_set), the buffers go through the pipeline: chunked host
+// -> device copy, kernel, device -> host copy, with consecutive chunks on
+// three rotating internal streams, so that one chunk's upload, another's
+// kernel and a third's download proceed at once.  The device side of the
+// pipeline uses only the caller's workspace.
+#include <atomic>
 #include <mutex>
 
 #include "trace.h"
@@ -23,6 +30,8 @@ constexpr int kMaxDevices = 64;
 
 // The route the calling thread's last sincos_pairs_host call took.
 thread_local int g_last_path = SINCOS_HOST_PATH_NONE;
+// The process-wide route policy (sincos_host_route_set).
+std::atomic<int> g_route_policy{SINCOS_HOST_ROUTE_AUTO};
 
 struct Pipe {
     bool ready = false;
@@ -52,18 +61,29 @@ int get_pipe(int dev, Pipe **out)
     return SINCOS_OK;
 }
 
-// Device address of a host buffer the GPU can access directly (page-locked
-// and mapped), or false (then the copy pipeline is used).
-bool mapped_host(const void *p, void **dev)
+// Device address of a host buffer the GPU can access directly: its mapped
+// address if it is page-locked and mapped, the host address itself if it is
+// pageable memory and the device reads pageable memory through the host's
+// page tables; else false (then the copy pipeline is used).  *pinned tells
+// which of the first two it was.
+bool reachable_host(const void *p, bool pageable_access, void **dev, bool *pinned)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
-    *dev = a.devicePointer;
-    return true;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        *dev = a.devicePointer;
+        *pinned = true;
+        return true;
+    }
+    if (a.type == cudaMemoryTypeUnregistered && pageable_access) {
+        *dev = const_cast<void *>(p);
+        *pinned = false;
+        return true;
+    }
+    return false;
 }
 
 // The zero-copy plan: the register path with 16-byte plain loads and
@@ -116,7 +136,11 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
     cudaStream_t user = (cudaStream_t)stream;
 
     void *xd = nullptr, *sd = nullptr, *cd = nullptr;
-    if (mapped_host(x_host, &xd) && mapped_host(s_host, &sd) && mapped_host(c_host, &cd)) {
+    bool px = false, ps = false, pc = false;
+    const bool pa = dev->pageable_access;
+    if (g_route_policy.load(std::memory_order_relaxed) == SINCOS_HOST_ROUTE_AUTO &&
+        reachable_host(x_host, pa, &xd, &px) && reachable_host(s_host, pa, &sd, &ps) &&
+        reachable_host(c_host, pa, &cd, &pc)) {
         // zero-copy: the same aliasing rules as sincos_pairs_ex
         const size_t xb = (size_t)n * 4, ob = (size_t)n * osz;
         bool in_place = false;
@@ -127,7 +151,8 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
         }
         rc = launch_forward((const float *)xd, sd, cd, n, out_dtype, reduction, coef, in_place,
                             kZeroCopyPlan, *dev, user);
-        if (rc == SINCOS_OK) g_last_path = SINCOS_HOST_PATH_ZERO_COPY;
+        if (rc == SINCOS_OK)
+            g_last_path = px && ps && pc ? SINCOS_HOST_PATH_ZERO_COPY : SINCOS_HOST_PATH_ZERO_COPY_PAGEABLE;
         return rc;
     }
 
@@ -172,5 +197,13 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
 }
 
 int sincos_host_last_path(void) { return g_last_path; }
+
+int sincos_host_route_set(int policy)
+{
+    if (policy != SINCOS_HOST_ROUTE_AUTO && policy != SINCOS_HOST_ROUTE_PIPELINE)
+        return SINCOS_EINVAL;
+    g_route_policy.store(policy, std::memory_order_relaxed);
+    return SINCOS_OK;
+}
 
 }  // extern "C"

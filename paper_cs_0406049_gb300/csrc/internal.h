@@ -17,6 +17,10 @@ struct DeviceInfo {
     int sms = 0;
     int major = 0, minor = 0;
     int max_threads_per_sm = 0;
+    // The device reads and writes pageable host memory coherently, through
+    // the host's page tables (cudaDevAttrPageableMemoryAccess; Grace systems
+    // over NVLink-C2C).
+    bool pageable_access = false;
     char name[256] = {0};
 };
 

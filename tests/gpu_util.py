@@ -89,3 +89,34 @@ class forced_plan:
         for b, p in self.saved:
             api.sincos_plan_set(self.op, self.dtype, 1 << b, p["block"], p["unroll"],
                                 p["ctas_per_sm"], p["vec_bytes"])
+
+
+def pageable_access(device: int = 0) -> bool:
+    """Whether the device reads pageable host memory through the host's page
+    tables (cudaDevAttrPageableMemoryAccess), asked of the CUDA runtime."""
+    import ctypes
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+        except OSError:
+            continue
+        v = ctypes.c_int(0)
+        if rt.cudaDeviceGetAttribute(ctypes.byref(v), ctypes.c_int(88), ctypes.c_int(device)) == 0:
+            return v.value == 1
+    return False
+
+
+class host_route:
+    """sincos_host_route_set inside a with block, back to "auto" after it."""
+
+    def __init__(self, policy: str):
+        self.policy = policy
+
+    def __enter__(self):
+        from paper_cs_0406049_gb300 import api
+        api.sincos_host_route_set(self.policy)
+        return self
+
+    def __exit__(self, *exc):
+        from paper_cs_0406049_gb300 import api
+        api.sincos_host_route_set("auto")

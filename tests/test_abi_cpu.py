@@ -118,6 +118,9 @@ def test_host_path_validation(lib):
     assert lib.sincos_pairs_host(A, A + 4096, A + 8192, 8, 0, 0, 0, ws, 64, None) == _lib.EINVAL
     assert lib.sincos_pairs_host(A, A + 4096, A + 4100, 8, 0, 0, 0, ws, 1 << 20, None) == _lib.EOVERLAP
     assert lib.sincos_host_last_path() == _lib.HOST_PATH_NONE     # refused calls took no route
+    assert lib.sincos_host_route_set(2) == _lib.EINVAL
+    assert lib.sincos_host_route_set(_lib.HOST_ROUTE_PIPELINE) == _lib.OK
+    assert lib.sincos_host_route_set(_lib.HOST_ROUTE_AUTO) == _lib.OK
     assert lib.sincos_host_workspace_bytes(0, 64) == 3 * 64 * 12
     assert lib.sincos_host_workspace_bytes(1, 65) == 3 * 128 * 8
     assert lib.sincos_host_workspace_bytes(5, 64) == 0

@@ -6,7 +6,8 @@ import pytest
 import torch
 
 import oracle
-from gpu_util import as_np, assert_16_parity, assert_f32_parity, mixed_angles
+from gpu_util import (as_np, assert_16_parity, assert_f32_parity, host_route, mixed_angles,
+                      pageable_access)
 from paper_cs_0406049_gb300 import api
 
 pytestmark = pytest.mark.gpu
@@ -14,8 +15,12 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 @pytest.mark.parametrize("pinned", [True, False])
-def test_host_path_chunks(cuda_lib, dtype, pinned):
-    """Many chunks (a small workspace), a ragged last chunk, host arrays."""
+@pytest.mark.parametrize("route", ["auto", "pipeline"])
+def test_host_path_chunks(cuda_lib, dtype, pinned, route):
+    """Many chunks (a small workspace), a ragged last chunk, host arrays;
+    every route: zero-copy on page-locked memory, zero-copy on pageable
+    memory where the device reaches it through the host's page tables (the
+    outputs are fresh, untouched pages), and the copy pipeline."""
     tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
     n = (1 << 20) + 12345
     x = mixed_angles(n, seed=9)
@@ -26,8 +31,15 @@ def test_host_path_chunks(cuda_lib, dtype, pinned):
         xh, sh, ch = xh.pin_memory(), sh.pin_memory(), ch.pin_memory()
     ws = torch.empty(api.sincos_host_workspace_bytes(dtype, 100000), dtype=torch.uint8,
                      device="cuda")
-    api.sincos_pairs_host(xh, sh, ch, ws, "compensated")
-    assert api.sincos_host_last_path() == ("zero-copy" if pinned else "pipeline")
+    with host_route(route):
+        api.sincos_pairs_host(xh, sh, ch, ws, "compensated")
+        got = api.sincos_host_last_path()
+    if route == "pipeline":
+        assert got == "pipeline"
+    elif pinned:
+        assert got == "zero-copy"
+    else:
+        assert got == ("zero-copy-pageable" if pageable_access() else "pipeline")
     torch.cuda.synchronize()
     want_s, want_c = oracle.sincos(x, reduction="compensated", out=dtype)
     if dtype == "f32":
@@ -38,9 +50,11 @@ def test_host_path_chunks(cuda_lib, dtype, pinned):
         assert_16_parity(as_np(ch), want_c, dtype == "bf16", "host c")
 
 
-def test_host_path_mixed_memory_kinds(cuda_lib):
-    """Page-locked x with pageable outputs goes through the chunked copies;
-    the results are the same."""
+@pytest.mark.parametrize("route", ["auto", "pipeline"])
+def test_host_path_mixed_memory_kinds(cuda_lib, route):
+    """Page-locked x and c with a pageable s: zero-copy where the device
+    reaches pageable memory (each buffer through its own address), the
+    chunked copies otherwise; the results are the same."""
     n = (1 << 19) + 77
     x = mixed_angles(n, seed=10)
     xh = torch.from_numpy(x).pin_memory()
@@ -48,8 +62,13 @@ def test_host_path_mixed_memory_kinds(cuda_lib):
     ch = torch.empty(n).pin_memory()
     ws = torch.empty(api.sincos_host_workspace_bytes("f32", 65536), dtype=torch.uint8,
                      device="cuda")
-    api.sincos_pairs_host(xh, sh, ch, ws)
-    assert api.sincos_host_last_path() == "pipeline"
+    with host_route(route):
+        api.sincos_pairs_host(xh, sh, ch, ws)
+        got = api.sincos_host_last_path()
+    if route == "auto" and pageable_access():
+        assert got == "zero-copy-pageable"
+    else:
+        assert got == "pipeline"
     torch.cuda.synchronize()
     want_s, want_c = oracle.sincos(x)
     assert_f32_parity(sh.numpy(), want_s, "mixed s")
