@@ -876,13 +876,17 @@ def run_ours(args, dist: Dist):
             # the same call on ordinary (pageable) host memory: what a caller
             # without page-locked buffers gets (zero-copy where the device
             # reaches pageable memory), and the copy pipeline on it for context
+            # (outputs written once by the CPU first: a page the GPU touches
+            # first is populated by that call, about 0.65 s for 2 GiB)
             xp = torch.from_numpy(x_np)
             sp, cp = torch.empty(n, dtype=torch.float32), torch.empty(n, dtype=torch.float32)
+            sp.fill_(0.0)
+            cp.fill_(0.0)
             for key, policy, p_steps in (("pageable", "auto", 5), ("pageable_pipeline", "pipeline", 3)):
                 api.sincos_host_route_set(policy)
                 try:
                     tp, _, _ = time_loop(torch, lambda: api.sincos_pairs_host(xp, sp, cp, ws),
-                                         p_steps, 1, dist)
+                                         p_steps, 2, dist)
                     route_p = api.sincos_host_last_path()
                 finally:
                     api.sincos_host_route_set("auto")

@@ -274,9 +274,12 @@ int sincos_batched_graph_destroy(sincos_graph g);
  *   (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping), and, on a
  *   device that accesses pageable memory through the host's page tables
  *   (cudaDevAttrPageableMemoryAccess, as GB300 with Grace), ordinary pageable
- *   memory too (pages the CPU has not touched yet are placed on first access
- *   by the system).  x may be s or c exactly (binary32 output); any other
- *   overlap returns SINCOS_EOVERLAP.
+ *   memory too.  Pageable pages that nothing has touched yet are populated
+ *   by the system on the kernel's first access, which makes that first call
+ *   slow (about 0.65 s for 2 GiB of fresh outputs on GB300; 12.4 ms per
+ *   2^28-angle call afterwards, the same as page-locked buffers).  x may be
+ *   s or c exactly (binary32 output); any other overlap returns
+ *   SINCOS_EOVERLAP.
  *   Otherwise, or under SINCOS_HOST_ROUTE_PIPELINE, x is copied to the device
  *   in chunks, each chunk is computed, and s and c are copied back, with
  *   copies and kernels of different chunks overlapped on internal streams
