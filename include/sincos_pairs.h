@@ -16,9 +16,13 @@
  *
  * Conventions shared by every entry point
  *   Memory     All array arguments are caller-owned.  Unless an entry point
- *              says otherwise they are device (or managed) memory of the
- *              current CUDA device.  No entry point allocates per call,
- *              except where stated (batched scratch, host-path streams).
+ *              says otherwise they are device memory of the current CUDA
+ *              device (cudaMalloc, or managed memory prefetched to that
+ *              device: the bulk kernels move data with the copy engine of
+ *              the SM, which is not used on pages that would first have to
+ *              migrate).  Host arrays go to sincos_pairs_host.  No entry
+ *              point allocates per call, except where stated (batched
+ *              scratch, host-path streams).
  *   Layout     Structure of arrays: one contiguous array of angles in, one of
  *              sines and one of cosines out (the paper's `struct phase` holds
  *              the two vectors separately).  Element i of every array belongs
