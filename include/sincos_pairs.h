@@ -353,11 +353,11 @@ typedef enum {
  * stage 8192-angle chunks through a two-stage shared-memory ring and bulk
  * stores write the results (192 KB of shared memory for binary32 outputs,
  * one CTA per SM); block is 128, 256, 512 or 1024 and unroll is not used.
- * For the single-array forward, ctas_per_sm >= 2 selects 4096-angle stages
- * instead (96 KB for binary32 and 64 KB for 16-bit outputs: two or three CTAs
- * per SM; block 128, 256 or 512); elsewhere ctas_per_sm is not used.  The
- * batched ring kernel runs min(block, 512) consumer threads plus one
- * producer warp.  Single arrays shorter than one chunk, and the backward kernel, use
+ * For the single-array forward and the batched ring kernel, ctas_per_sm >= 2
+ * selects 4096-angle stages instead (96 KB for binary32 and 64 KB for 16-bit
+ * outputs: two or three CTAs per SM as registers allow; block 128, 256 or
+ * 512); for exp(ix) ctas_per_sm is not used.  The batched ring kernel runs
+ * min(block, 512) consumer threads plus one producer warp.  Single arrays shorter than one chunk, and the backward kernel, use
  * the 16-byte register path instead. */
 typedef struct {
     int block;        /* 64 .. 1024, multiple of 32 */

@@ -61,10 +61,15 @@ struct RingPart {
     int edge0;             // index of the part's first edge within the stage
 };
 
-template <class OutT>
+// Stage capacity of the small-stage variant (plans with ctas_per_sm >= 2):
+// half the angles per stage, so that two (binary32) or three (16-bit
+// outputs) CTAs share an SM, as the single-array kernel's small stages do.
+constexpr int kRingSmallCap = kBulkSmallChunk;
+
+template <class OutT, int CAP = kRingCap>
 constexpr size_t ring_smem_bytes()
 {
-    return (size_t)kRingStages * kRingCap * 4 + 2 * 2 * (size_t)kRingCap * sizeof(OutT);
+    return (size_t)kRingStages * CAP * 4 + 2 * 2 * (size_t)CAP * sizeof(OutT);
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
@@ -282,7 +287,7 @@ __device__ __forceinline__ int64_t ring_tile_lo(int64_t k, int h)
 // parts that fill each stage to kRingCap angles (a range that does not fit is
 // split on a 32-angle boundary of its grid), so every stage but the last
 // carries a full load however the segments are sized.
-template <class OutT>
+template <class OutT, int CAP>
 __device__ __forceinline__ void ring_producer(const sincos_seg *segs, const int64_t *lens,
                                               int count, const RingRun run, float *xin,
                                               RingPart (*parts)[kRingMaxParts], int *nparts,
@@ -356,7 +361,7 @@ __device__ __forceinline__ void ring_producer(const sincos_seg *segs, const int6
             else if (h == -1) u0 = pos + (((4u - ((unsigned)((uintptr_t)(x + pos) & 15u) >> 2)) & 3u));
             else u0 = rhi;
             if (u0 > rhi) u0 = rhi;
-            const int64_t avail = kRingCap - cap;
+            const int64_t avail = CAP - cap;
             int64_t u1 = u0 + (rhi - u0) / E * E, hi = rhi;
             if (u1 - u0 > avail) {
                 const int64_t take = avail / kSplit * kSplit;
@@ -402,7 +407,7 @@ __device__ __forceinline__ void ring_producer(const sincos_seg *segs, const int6
         if (lane == 0) {
             const uint32_t bar = smem_addr(&full[st]);
             if (cap > 0) mbar_expect_tx(bar, (uint32_t)cap * 4u);
-            float *dst = xin + (size_t)st * kRingCap;
+            float *dst = xin + (size_t)st * CAP;
             for (int i = 0; i < n; ++i) {
                 const RingPart &p = parts[slot][i];
                 const int need = p.u1 - p.u0;
@@ -426,7 +431,7 @@ __device__ __forceinline__ void ring_producer(const sincos_seg *segs, const int6
     }
 }
 
-template <class OutT, int RED, int COEF, int NT>
+template <class OutT, int RED, int COEF, int NT, int CAP>
 __global__ void __launch_bounds__(NT + 32)
 k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
 {
@@ -434,8 +439,8 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
     constexpr int kEdgeRegs = 4;
     extern __shared__ __align__(128) unsigned char smem[];
     float *xin = (float *)smem;                                        // [stages][cap]
-    OutT *sout = (OutT *)(xin + kRingStages * kRingCap);                // [2][cap]
-    OutT *cout = sout + 2 * kRingCap;                                   // [2][cap]
+    OutT *sout = (OutT *)(xin + kRingStages * CAP);                     // [2][cap]
+    OutT *cout = sout + 2 * CAP;                                        // [2][cap]
     __shared__ RingPart parts[kRingSlots][kRingMaxParts];
     __shared__ int nparts[kRingSlots], nedges[kRingSlots], nmid[kRingSlots], nout[kRingSlots];
     __shared__ __align__(8) uint64_t full[kRingStages], empty[kRingStages];
@@ -464,8 +469,8 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
     __syncthreads();
 
     if (tid >= NT) {
-        ring_producer<OutT>(segs, lens, count, run, xin, parts, nparts, nedges, nmid, nout,
-                            full, empty, &give_up);
+        ring_producer<OutT, CAP>(segs, lens, count, run, xin, parts, nparts, nedges, nmid, nout,
+                                 full, empty, &give_up);
         return;
     }
 
@@ -485,9 +490,9 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
         const int n = nparts[slot];
         if (n < 0) break;
         const RingPart *pp = parts[slot];
-        const float *xs = xin + (size_t)st * kRingCap;
-        OutT *so = sout + (size_t)b * kRingCap;
-        OutT *co = cout + (size_t)b * kRingCap;
+        const float *xs = xin + (size_t)st * CAP;
+        OutT *so = sout + (size_t)b * CAP;
+        OutT *co = cout + (size_t)b * CAP;
 
         // Edges: issue the first loads now, use them after the middles.
         const int ne = nedges[slot];
@@ -518,7 +523,7 @@ k_batched_ring(const sincos_seg *segs, const int64_t *lens, int count)
         const int mid = nmid[slot];
         if (nout[slot] == mid) {
 #pragma unroll
-            for (int j = 0; j < kRingCap / (NT * E); ++j) {
+            for (int j = 0; j < CAP / (NT * E); ++j) {
                 const int e = (j * NT + tid) * E;
                 if (e < mid) bulk_tile_vec<RED, COEF, OutT, kPack>(xs, so, co, e);
             }
@@ -595,26 +600,33 @@ static inline int ring_consumers(int block)
     return block == 128 ? 128 : block >= 512 ? 512 : 256;
 }
 
-template <class OutT, int RED, int COEF>
-static const void *ring_kernel_rc(int nt)
+template <class OutT, int RED, int COEF, int CAP>
+static const void *ring_kernel_cap(int nt)
 {
     switch (nt) {
-    case 128: return (const void *)k_batched_ring<OutT, RED, COEF, 128>;
-    case 512: return (const void *)k_batched_ring<OutT, RED, COEF, 512>;
-    default: return (const void *)k_batched_ring<OutT, RED, COEF, 256>;
+    case 128: return (const void *)k_batched_ring<OutT, RED, COEF, 128, CAP>;
+    case 512: return (const void *)k_batched_ring<OutT, RED, COEF, 512, CAP>;
+    default: return (const void *)k_batched_ring<OutT, RED, COEF, 256, CAP>;
     }
 }
 
+template <class OutT, int RED, int COEF>
+static const void *ring_kernel_rc(int nt, bool small)
+{
+    return small ? ring_kernel_cap<OutT, RED, COEF, kRingSmallCap>(nt)
+                 : ring_kernel_cap<OutT, RED, COEF, kRingCap>(nt);
+}
+
 template <class OutT>
-static const void *ring_kernel_t(int red, int coef, int nt)
+static const void *ring_kernel_t(int red, int coef, int nt, bool small)
 {
     if (red == RED_PLAIN && coef == COEF_NORMALIZED)
-        return ring_kernel_rc<OutT, RED_PLAIN, COEF_NORMALIZED>(nt);
+        return ring_kernel_rc<OutT, RED_PLAIN, COEF_NORMALIZED>(nt, small);
     if (red == RED_COMPENSATED && coef == COEF_NORMALIZED)
-        return ring_kernel_rc<OutT, RED_COMPENSATED, COEF_NORMALIZED>(nt);
+        return ring_kernel_rc<OutT, RED_COMPENSATED, COEF_NORMALIZED>(nt, small);
     if (red == RED_PLAIN && coef == COEF_DAGGER)
-        return ring_kernel_rc<OutT, RED_PLAIN, COEF_DAGGER>(nt);
-    return ring_kernel_rc<OutT, RED_COMPENSATED, COEF_DAGGER>(nt);
+        return ring_kernel_rc<OutT, RED_PLAIN, COEF_DAGGER>(nt, small);
+    return ring_kernel_rc<OutT, RED_COMPENSATED, COEF_DAGGER>(nt, small);
 }
 
 
@@ -624,8 +636,11 @@ static int launch_batched_ring(const sincos_seg *segs, const int64_t *lens, int 
                                const DeviceInfo &dev, cudaStream_t st)
 {
     const int block = ring_consumers(plan.block);
-    const void *fn = ring_kernel_t<OutT>(red, coef, block);
-    constexpr size_t smem = ring_smem_bytes<OutT>();
+    // ctas_per_sm >= 2 asks for the small-stage variant, as for the
+    // single-array bulk kernel
+    const bool small = plan.ctas_per_sm >= 2;
+    const void *fn = ring_kernel_t<OutT>(red, coef, block, small);
+    const size_t smem = small ? ring_smem_bytes<OutT, kRingSmallCap>() : ring_smem_bytes<OutT>();
     const int per_sm = bulk_resident_ctas(fn, block + 32, smem);
     if (per_sm <= 0) return SINCOS_EUNSUPPORTED;
     const int grid = batched_grid(per_sm, dev);

@@ -52,13 +52,17 @@ sincos_plan default_plan(int op, int dtype)
     // The single-array forward defaults to the bulk (TMA-staged) path: 8192-
     // angle stages for binary32, 4096-angle stages (three CTAs per SM) for
     // 16-bit outputs, which with programmatic dependent launch beat the
-    // 32-byte register path (6480 against 6350 GB/s at 2^26).  Batched
-    // 16-bit outputs keep the register path.
+    // 32-byte register path (6480 against 6350 GB/s at 2^26).  The batched
+    // ring kernel likewise runs 4096-angle stages for binary32 (two CTAs per
+    // SM: 6410 against 6256 GB/s plain, 6391 against 6111 compensated on the
+    // 4096-array workload); batched 16-bit outputs keep the register path
+    // (5740-5860 GB/s; the small-stage ring gave 6000 plain but 5555
+    // compensated).
     if (op == SINCOS_OP_BACKWARD) return sincos_plan{512, 2, 2, 16};
     if (op == SINCOS_OP_EXPI) return sincos_plan{512, 2, 1, 0};
     if (op == SINCOS_OP_HUYGENS) return sincos_plan{256, 1, 8, 32};
     if (op == SINCOS_OP_BATCHED)
-        return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{256, 2, 4, 32};
+        return dtype == SINCOS_F32 ? sincos_plan{512, 2, 2, 0} : sincos_plan{1024, 2, 1, 16};
     return dtype == SINCOS_F32 ? sincos_plan{512, 2, 1, 0} : sincos_plan{512, 2, 3, 0};
 }
 
@@ -169,7 +173,7 @@ std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
     }
     if (op != SINCOS_OP_BACKWARD)   // bulk path: one CTA per SM, CTA size only
         for (int block : {128, 256, 512, 1024}) out.push_back(sincos_plan{block, 2, 1, 0});
-    if (op == SINCOS_OP_PAIRS)      // bulk path with 4096-angle stages, several CTAs per SM
+    if (op == SINCOS_OP_PAIRS || op == SINCOS_OP_BATCHED)   // 4096-angle stages, several CTAs per SM
         for (int block : {128, 256, 512}) out.push_back(sincos_plan{block, 2, 2, 0});
     const int max_threads = dev.max_threads_per_sm > 0 ? dev.max_threads_per_sm : 2048;
     for (int vec : {16, 32})

@@ -37,8 +37,8 @@ def check_all(x, s, c, dtype, red, coef, what):
 
 EDGE_LENS = [1, 0, 3, 4095, 4096, 4097, 8191, 8192, 8193, 2, 65536 + 17, 5, 0, 0, 1, 1 << 20,
              31, 7, 8, 3 * 8192 + 63, 64, 65]
-PATHS = {"bulk256": (256, 2, 1, 0), "bulk1024": (1024, 2, 1, 0), "reg16": (1024, 2, 1, 16),
-         "reg32": (256, 4, 8, 32)}
+PATHS = {"bulk256": (256, 2, 1, 0), "bulk1024": (1024, 2, 1, 0), "bulksmall": (256, 2, 3, 0),
+         "reg16": (1024, 2, 1, 16), "reg32": (256, 4, 8, 32)}
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
