@@ -152,7 +152,8 @@ int sincos_pairs_host(const float *x_host, void *s_host, void *c_host, int64_t n
         rc = launch_forward((const float *)xd, sd, cd, n, out_dtype, reduction, coef, in_place,
                             kZeroCopyPlan, *dev, user);
         if (rc == SINCOS_OK)
-            g_last_path = px && ps && pc ? SINCOS_HOST_PATH_ZERO_COPY : SINCOS_HOST_PATH_ZERO_COPY_PAGEABLE;
+            g_last_path = px && ps && pc ? SINCOS_HOST_PATH_ZERO_COPY
+                                         : SINCOS_HOST_PATH_ZERO_COPY_PAGEABLE;
         return rc;
     }
 
