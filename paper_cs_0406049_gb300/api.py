@@ -22,20 +22,56 @@ _OPS = {"pairs": _lib.OP_PAIRS, "backward": _lib.OP_BACKWARD, "batched": _lib.OP
         "expi": _lib.OP_EXPI, "huygens": _lib.OP_HUYGENS}
 
 
+_loaded = None
+
+
 def lib():
-    return _lib.load()
+    global _loaded
+    if _loaded is None:
+        _loaded = _lib.load()
+    return _loaded
 
 
 def _torch_dtype(d) -> torch.dtype:
     return _DTYPE_NAMES[d] if isinstance(d, str) else d
 
 
+# The raw handle of a device's current stream.  PyTorch's own accessor for it
+# avoids building a Stream object on every call (2 us of host time per call,
+# as much as the rest of a small launch); the public route is the fallback.
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream, device) -> int:
     if stream is None:
+        index = device.index if isinstance(device, torch.device) else device
+        if _raw_stream is not None and index is not None:
+            return _raw_stream(index)
         return torch.cuda.current_stream(device).cuda_stream
     if isinstance(stream, torch.cuda.Stream):
         return stream.cuda_stream
     return int(stream)
+
+
+class _on_device:
+    """Make `device` current for a library call (the C ABI acts on the
+    calling thread's current device); switches only when it is not current
+    already, which costs far less than torch.cuda.device's full context."""
+
+    __slots__ = ("index", "prev")
+
+    def __init__(self, device):
+        self.index = device.index if isinstance(device, torch.device) else device
+
+    def __enter__(self):
+        self.prev = torch.cuda.current_device()
+        if self.index is not None and self.index != self.prev:
+            torch.cuda.set_device(self.index)
+        return self
+
+    def __exit__(self, *exc):
+        if self.index is not None and self.index != self.prev:
+            torch.cuda.set_device(self.prev)
 
 
 def _dev(t: torch.Tensor, name: str, dtype=None) -> int:
@@ -67,7 +103,7 @@ def sincos_pairs(x: torch.Tensor, s: torch.Tensor, c: torch.Tensor, stream=None)
     n = x.numel()
     if s.numel() != n or c.numel() != n:
         raise ValueError("x, s and c must have the same number of elements")
-    with torch.cuda.device(x.device):
+    with _on_device(x.device):
         check(lib().sincos_pairs(_dev(x, "x", torch.float32), _dev(s, "s", torch.float32),
                                  _dev(c, "c", torch.float32), n, _stream(stream, x.device)),
               "sincos_pairs")
@@ -79,7 +115,7 @@ def sincos_pairs_ex(x: torch.Tensor, s: torch.Tensor, c: torch.Tensor, reduction
     n = x.numel()
     if s.numel() != n or c.numel() != n or s.dtype != c.dtype:
         raise ValueError("s and c must match x in size and each other in dtype")
-    with torch.cuda.device(x.device):
+    with _on_device(x.device):
         check(lib().sincos_pairs_ex(_dev(x, "x", torch.float32), _dev(s, "s"), _dev(c, "c"), n,
                                     _DTYPES[s.dtype], _REDUCTIONS[reduction], _COEFS[coef],
                                     _stream(stream, x.device)),
@@ -94,7 +130,7 @@ def sincos_expi(x: torch.Tensor, z: torch.Tensor, reduction: str = "plain",
     zf = torch.view_as_real(z) if z.is_complex() else z
     if zf.dtype != torch.float32 or zf.numel() != 2 * n:
         raise ValueError("z must be complex64 with x's size, or float32 with twice it")
-    with torch.cuda.device(x.device):
+    with _on_device(x.device):
         check(lib().sincos_expi(_dev(x, "x", torch.float32), _dev(zf, "z"), n,
                                 _REDUCTIONS[reduction], _COEFS[coef], _stream(stream, x.device)),
               "sincos_expi")
@@ -128,7 +164,7 @@ def sincos_huygens(p, q, a: torch.Tensor, k: float, u: torch.Tensor,
     """u_i = sum_j a_j exp(i k |p_i - q_j|) / |p_i - q_j|; p and q are (x, y, z)
     triples of float32 CUDA tensors, a complex (or real) amplitudes."""
     ptrs, m, n, up, keep = _huygens_args(p, q, a, u)
-    with torch.cuda.device(u.device):
+    with _on_device(u.device):
         check(lib().sincos_huygens(ptrs[0], ptrs[1], ptrs[2], m, ptrs[3], ptrs[4], ptrs[5],
                                    ptrs[6], ptrs[7], n, float(k), _REDUCTIONS[reduction], up,
                                    _stream(stream, u.device)), "sincos_huygens")
@@ -146,7 +182,7 @@ def sincos_autotune_huygens(p, q, a, k: float, u, reduction: str = "compensated"
                             stream=None) -> dict:
     ptrs, m, n, up, keep = _huygens_args(p, q, a, u)
     plan = _lib.sincos_plan()
-    with torch.cuda.device(u.device):
+    with _on_device(u.device):
         check(lib().sincos_autotune_huygens(ptrs[0], ptrs[1], ptrs[2], m, ptrs[3], ptrs[4],
                                             ptrs[5], ptrs[6], ptrs[7], n, float(k),
                                             _REDUCTIONS[reduction], up,
@@ -163,7 +199,7 @@ def sincos_backward(gs, gc, s: torch.Tensor, c: torch.Tensor, gx: torch.Tensor,
     for t in (gs, gc, s, c):
         if t is not None and t.numel() != n:
             raise ValueError("all arrays must have the same number of elements")
-    with torch.cuda.device(gx.device):
+    with _on_device(gx.device):
         check(lib().sincos_backward(
             None if gs is None else _dev(gs, "gs", torch.float32),
             None if gc is None else _dev(gc, "gc", torch.float32),
@@ -204,7 +240,7 @@ def sincos_batched(segs: torch.Tensor, lens: torch.Tensor, out_dtype="f32",
     """All segments at once: one self-scheduling launch with the binary32
     default plan, a schedule kernel and a tile kernel with register plans."""
     count = lens.numel()
-    with torch.cuda.device(lens.device):
+    with _on_device(lens.device):
         check(lib().sincos_batched_ex(_dev(segs, "segs"), _dev(lens, "lens", torch.int64), count,
                                       _DTYPES[_torch_dtype(out_dtype)], _REDUCTIONS[reduction],
                                       _COEFS[coef], _stream(stream, lens.device)),
@@ -219,7 +255,7 @@ def sincos_batched_noalloc(segs: torch.Tensor, lens: torch.Tensor, out_dtype="f3
     calls; at most ``NOALLOC_MAX_SEGMENTS`` arrays; calls must not overlap on
     the GPU)."""
     count = lens.numel()
-    with torch.cuda.device(lens.device):
+    with _on_device(lens.device):
         check(lib().sincos_batched_noalloc(_dev(segs, "segs"), _dev(lens, "lens", torch.int64),
                                            count, _DTYPES[_torch_dtype(out_dtype)],
                                            _REDUCTIONS[reduction], _COEFS[coef],
@@ -239,14 +275,14 @@ class BatchedGraph:
         self._keep = (segs, lens)
         self.device = lens.device
         self._h = ctypes.c_void_p()
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             check(lib().sincos_batched_graph_create(
                 _dev(segs, "segs"), _dev(lens, "lens", torch.int64), lens.numel(),
                 _DTYPES[_torch_dtype(out_dtype)], _REDUCTIONS[reduction], _COEFS[coef],
                 ctypes.byref(self._h)), "sincos_batched_graph_create")
 
     def launch(self, stream=None) -> None:
-        with torch.cuda.device(self.device):
+        with _on_device(self.device):
             check(lib().sincos_batched_graph_launch(self._h, _stream(stream, self.device)),
                   "sincos_batched_graph_launch")
 
@@ -280,7 +316,7 @@ def sincos_pairs_host(x_host: torch.Tensor, s_host: torch.Tensor, c_host: torch.
     if s_host.numel() != n or c_host.numel() != n or s_host.dtype != c_host.dtype:
         raise ValueError("s_host and c_host must match x_host in size and each other in dtype")
     ws = _dev(workspace, "workspace")
-    with torch.cuda.device(workspace.device):
+    with _on_device(workspace.device):
         check(lib().sincos_pairs_host(
             _host(x_host, "x_host", torch.float32), _host(s_host, "s_host"),
             _host(c_host, "c_host"), n, _DTYPES[s_host.dtype], _REDUCTIONS[reduction],
@@ -329,7 +365,7 @@ def sincos_plan_set(op: str, out_dtype, n: int, block: int, unroll: int, ctas_pe
 def sincos_autotune_pairs(x, s, c, reduction: str = "plain", coef: str = "normalized",
                           stream=None) -> dict:
     p = _lib.sincos_plan()
-    with torch.cuda.device(x.device):
+    with _on_device(x.device):
         check(lib().sincos_autotune_pairs(
             _dev(x, "x", torch.float32), _dev(s, "s"), _dev(c, "c"), x.numel(),
             _DTYPES[s.dtype], _REDUCTIONS[reduction], _COEFS[coef], _stream(stream, x.device),
@@ -341,7 +377,7 @@ def sincos_autotune_expi(x, z, reduction: str = "plain", coef: str = "normalized
                          stream=None) -> dict:
     p = _lib.sincos_plan()
     zf = torch.view_as_real(z) if z.is_complex() else z
-    with torch.cuda.device(x.device):
+    with _on_device(x.device):
         check(lib().sincos_autotune_expi(_dev(x, "x", torch.float32), _dev(zf, "z"), x.numel(),
                                          _REDUCTIONS[reduction], _COEFS[coef],
                                          _stream(stream, x.device), ctypes.byref(p)),
@@ -351,7 +387,7 @@ def sincos_autotune_expi(x, z, reduction: str = "plain", coef: str = "normalized
 
 def sincos_autotune_backward(gs, gc, s, c, gx, stream=None) -> dict:
     p = _lib.sincos_plan()
-    with torch.cuda.device(gx.device):
+    with _on_device(gx.device):
         check(lib().sincos_autotune_backward(
             None if gs is None else _dev(gs, "gs", torch.float32),
             None if gc is None else _dev(gc, "gc", torch.float32),
@@ -364,7 +400,7 @@ def sincos_autotune_backward(gs, gc, s, c, gx, stream=None) -> dict:
 def sincos_autotune_batched(segs, lens, out_dtype="f32", reduction: str = "plain",
                             coef: str = "normalized", stream=None) -> dict:
     p = _lib.sincos_plan()
-    with torch.cuda.device(lens.device):
+    with _on_device(lens.device):
         check(lib().sincos_autotune_batched(
             _dev(segs, "segs"), _dev(lens, "lens", torch.int64), lens.numel(),
             _DTYPES[_torch_dtype(out_dtype)], _REDUCTIONS[reduction], _COEFS[coef],
