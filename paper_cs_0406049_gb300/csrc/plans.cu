@@ -6,6 +6,7 @@
 // output dtype and the bit length of the element count, so one tuning run
 // per size class covers every later call in that class.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -27,6 +28,9 @@ using PlanKey = std::tuple<std::string, int, int, int>;   // device, op, dtype, 
 
 std::mutex g_plan_mu;
 std::map<PlanKey, sincos_plan> g_plans;
+// Bumped on every change of g_plans; a thread's last lookup (plan_for) stays
+// valid while it is unchanged.
+std::atomic<uint64_t> g_plans_version{0};
 std::once_flag g_env_once;
 
 int bucket_of(int64_t n)
@@ -153,6 +157,7 @@ int load_file(const char *path)
     }
     std::lock_guard<std::mutex> lock(g_plan_mu);
     for (auto &kv : loaded) g_plans[kv.first] = kv.second;
+    g_plans_version.fetch_add(1, std::memory_order_release);
     return SINCOS_OK;
 }
 
@@ -160,6 +165,7 @@ void store_plan(const DeviceInfo &dev, int op, int dtype, int64_t n, const sinco
 {
     std::lock_guard<std::mutex> lock(g_plan_mu);
     g_plans[PlanKey(device_key(dev), op, dtype, bucket_of(n))] = p;
+    g_plans_version.fetch_add(1, std::memory_order_release);
 }
 
 std::vector<sincos_plan> candidates(const DeviceInfo &dev, int op)
@@ -314,9 +320,27 @@ bool plan_valid(const sincos_plan &p)
 sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n)
 {
     std::call_once(g_env_once, load_env_cache);
-    std::lock_guard<std::mutex> lock(g_plan_mu);
-    auto it = g_plans.find(PlanKey(device_key(dev), op, dtype, bucket_of(n)));
-    return it != g_plans.end() ? it->second : default_plan(op, dtype);
+    // Repeated calls of one kind (the common case) reuse the calling
+    // thread's last answer while no plan has changed since.
+    struct Last {
+        uint64_t version = ~0ull;
+        int ordinal = -1, op = -1, dtype = -1, bucket = -1;
+        sincos_plan plan{};
+    };
+    thread_local Last last;
+    const int bucket = bucket_of(n);
+    const uint64_t version = g_plans_version.load(std::memory_order_acquire);
+    if (last.version == version && last.ordinal == dev.ordinal && last.op == op &&
+        last.dtype == dtype && last.bucket == bucket)
+        return last.plan;
+    sincos_plan p;
+    {
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        auto it = g_plans.find(PlanKey(device_key(dev), op, dtype, bucket));
+        p = it != g_plans.end() ? it->second : default_plan(op, dtype);
+    }
+    last = Last{version, dev.ordinal, op, dtype, bucket, p};
+    return p;
 }
 
 // Defined in batched_api.cu: per-(device, stream) prefix scratch.
