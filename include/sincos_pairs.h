@@ -196,13 +196,14 @@ int sincos_seg_check(const sincos_seg *seg, int64_t len, int out_dtype);
 
 /* The forward over `count` independent arrays: the method of Sec.
  * Methodology and Fig. 1 applied to each array (batching itself is not in
- * the paper).  Same per-element arithmetic as sincos_pairs_ex.  With the default plan for binary32 outputs this is one
- * persistent launch.  Each CTA derives its own contiguous run of the
- * concatenated element space from the lengths (equal work per CTA to within
- * one 8192-angle tile), then streams it through a TMA-staged ring.  With a
- * register plan (the default for 16-bit outputs) it is two launches: a small
- * schedule kernel over the lengths into the scratch below, then the tile
- * kernel.
+ * the paper).  Same per-element arithmetic as sincos_pairs_ex.  With the
+ * default plan for binary32 outputs this is one persistent launch.  Each CTA
+ * derives its own contiguous run of the concatenated element space from the
+ * lengths (equal work per CTA to within one 8192-angle tile), then streams it
+ * through a TMA-staged ring (4096-angle stages, two CTAs per SM, by default).
+ * With a register plan (the default for 16-bit outputs) it is two launches: a
+ * small schedule kernel over the lengths into the scratch below, then the
+ * tile kernel.
  *   segs  device array of `count` descriptors, read by the kernels.
  *   lens  device array of `count` int64 lengths; a negative length counts
  *         as 0.  Both arrays are read when the kernels run, so they may be
@@ -211,8 +212,9 @@ int sincos_seg_check(const sincos_seg *seg, int64_t len, int out_dtype);
  * (not checked: the descriptors live on the device).
  * Scratch (used by register plans): the library keeps one small device
  * buffer (count + 8195 int64) per (device, stream) pair, allocated with
- * cudaMalloc on the first call that needs a larger one.  A call that would allocate while `stream` is being
- * captured returns SINCOS_ECAPTURE; make one uncaptured call first.
+ * cudaMalloc on the first call that needs a larger one.  A call that would
+ * allocate while `stream` is being captured returns SINCOS_ECAPTURE; make one
+ * uncaptured call first.
  * sincos_batched_release() frees all such buffers (call it only when no
  * batched work is in flight). */
 int sincos_batched(const sincos_seg *segs, const int64_t *lens, int count,
@@ -257,8 +259,11 @@ int sincos_batched_noalloc(const sincos_seg *segs, const int64_t *lens, int coun
 
 /* A batched launch captured once into a CUDA graph and replayed (launch
  * infrastructure around the batched form of Sec. Methodology / Fig. 1; no
- * paper counterpart).  The graph owns its scratch, if its plan needs one; the segs/lens device arrays are read at every replay,
- * so their contents (not their addresses) may change between replays. */
+ * paper counterpart).  The graph owns its scratch, if its plan needs one;
+ * the segs/lens device arrays are read at every replay, so their contents
+ * (not their addresses) may change between replays.  A replay launches the
+ * kernels the graph holds (one for a ring plan, two for a register plan), and
+ * sincos_launch_count() counts them at each replay, not at creation. */
 typedef struct sincos_graph_s *sincos_graph;
 int sincos_batched_graph_create(const sincos_seg *segs, const int64_t *lens, int count,
                                 int out_dtype, int reduction, int coef, sincos_graph *out);
@@ -357,8 +362,9 @@ typedef enum {
  * selects 4096-angle stages instead (96 KB for binary32 and 64 KB for 16-bit
  * outputs: two or three CTAs per SM as registers allow; block 128, 256 or
  * 512); for exp(ix) ctas_per_sm is not used.  The batched ring kernel runs
- * min(block, 512) consumer threads plus one producer warp.  Single arrays shorter than one chunk, and the backward kernel, use
- * the 16-byte register path instead. */
+ * min(block, 512) consumer threads plus one producer warp.  Single arrays
+ * shorter than one chunk, and the backward kernel, use the 16-byte register
+ * path instead. */
 typedef struct {
     int block;        /* 64 .. 1024, multiple of 32 */
     int unroll;       /* 1, 2, 4 or 8 */
