@@ -305,3 +305,20 @@ def test_null_pointers_on_empty_arrays(cuda_lib, path):
         api.sincos_batched(segs.view(-1), lens_t)
     check_all(x, s, c, "f32", "plain", "normalized", f"null empties {path}")
     assert api.sincos_device_bad_segments() == 0
+
+
+def test_plan_change_takes_effect_on_the_next_call(cuda_lib):
+    """A plan set between two calls of the same kind is used by the second
+    (the library keeps each thread's last plan lookup until a plan changes):
+    a register plan launches two kernels, the ring plan one."""
+    lens = [7000, 3, 9000, 0, 12]
+    x, xt, s, c, offs = packed(lens, "f32", seed=8)
+    segs, lens_t = api.segments(xt, s, c, offs, lens)
+    for plan, kernels in ((PATHS["reg16"], 2), (PATHS["bulksmall"], 1), (PATHS["reg32"], 2),
+                          (PATHS["bulk256"], 1)):
+        with forced_plan("batched", "f32", plan):
+            before = api.sincos_launch_count()
+            api.sincos_batched(segs, lens_t)
+            torch.cuda.synchronize()
+            assert api.sincos_launch_count() - before == kernels, plan
+        check_all(x, s, c, "f32", "plain", "normalized", f"plan {plan}")
