@@ -88,6 +88,9 @@ bool reachable_host(const void *p, bool pageable_access, void **dev, bool *pinne
 
 // The zero-copy plan: the register path with 16-byte plain loads and
 // stores (every plan of that path measured the same over the host link).
+// Host memory is only ever touched by such loads and stores: the bulk
+// (TMA-staged) kernels are for device memory, and this plan never selects
+// them.
 constexpr sincos_plan kZeroCopyPlan = {256, 4, 4, 16};
 
 int64_t slot_elems_for(int dtype, size_t ws_bytes)
