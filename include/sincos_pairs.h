@@ -374,7 +374,10 @@ typedef struct {
 
 /* The plan used for (op, out_dtype, n) on the current device: the tuned one
  * if the cache holds it for n's power-of-two bucket, else the default.  For
- * SINCOS_OP_BATCHED, n is the segment count. */
+ * SINCOS_OP_BATCHED, n is the segment count.  The default for
+ * SINCOS_OP_PAIRS depends on n: {256, 2, 2, 0} (4096-angle stages) below 2^24
+ * angles, else {512, 2, 1, 0} for binary32 and {512, 2, 3, 0} for 16-bit
+ * outputs; the other operations' defaults do not depend on n. */
 int sincos_plan_get(int op, int out_dtype, int64_t n, sincos_plan *plan);
 /* Store a plan for (op, out_dtype, n's bucket) on the current device. */
 int sincos_plan_set(int op, int out_dtype, int64_t n, const sincos_plan *plan);

@@ -48,8 +48,20 @@ std::string device_key(const DeviceInfo &dev)
     return std::string(dev.name) + ":" + std::to_string(dev.sms);
 }
 
-sincos_plan default_plan(int op, int dtype)
+// Single arrays below 2^24 angles (power-of-two buckets up to 24) run the
+// 4096-angle stages with 256-thread CTAs, several per SM, for every output
+// type.  The big stages of the large-array default leave a partial last round
+// there (2^22 binary32 angles: 512 chunks on 152 SMs).  A GB300 sweep in
+// quarter-octave steps from 2^18 to 2^26 angles, against the large-array
+// defaults (geometric mean of the ratios; back-to-back calls / L2 flushed
+// between calls): 2^21..2^24 binary32 1.09 / 1.09, 16-bit 1.07-1.08 / 1.02;
+// 2^18..2^21 binary32 1.01 / 1.14, 16-bit 1.01 / 1.02; 2^24..2^26 binary32
+// 0.96 / 0.99 and 16-bit 0.99 / 1.00-1.01, where the defaults stay.
+constexpr int kSmallStageBuckets = 24;
+
+sincos_plan default_plan(int op, int dtype, int bucket)
 {
+    if (op == SINCOS_OP_PAIRS && bucket <= kSmallStageBuckets) return sincos_plan{256, 2, 2, 0};
     // Fastest plans of a GB300 sweep (2^26..2^28 elements, 4096-array batch).
     // About 1024 resident threads per SM with 2..8 vectors in flight each
     // beat full occupancy: fewer concurrent streams keep DRAM pages open.
@@ -337,7 +349,7 @@ sincos_plan plan_for(const DeviceInfo &dev, int op, int dtype, int64_t n)
     {
         std::lock_guard<std::mutex> lock(g_plan_mu);
         auto it = g_plans.find(PlanKey(device_key(dev), op, dtype, bucket));
-        p = it != g_plans.end() ? it->second : default_plan(op, dtype);
+        p = it != g_plans.end() ? it->second : default_plan(op, dtype, bucket);
     }
     last = Last{version, dev.ordinal, op, dtype, bucket, p};
     return p;

@@ -177,3 +177,51 @@ def test_autotune_backward_and_batched(cuda_lib):
     api.sincos_batched(segs, lens_t)
     want_s, _ = oracle.sincos(x)
     assert_f32_parity(as_np(s), want_s, "batched after tuning")
+
+
+_DEFAULTS = """
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_cs_0406049_gb300 import api, build
+build.build()
+out = {{}}
+for op in ("pairs", "expi", "backward", "batched"):
+    for dt in ("f32", "bf16", "f16"):
+        if op in ("expi", "backward") and dt != "f32":
+            continue
+        for lg in (0, 12, 20, 23, 24, 28):
+            for n in ((1 << lg) - 1, 1 << lg):
+                p = api.sincos_plan_get(op, dt, n)
+                out[f"{{op}} {{dt}} {{n}}"] = [p["block"], p["unroll"], p["ctas_per_sm"],
+                                            p["vec_bytes"]]
+print("PLANS", json.dumps(out))
+"""
+
+
+def test_default_plans_by_size(cuda_lib):
+    """A fresh process with no plan cache: single arrays below 2^24 angles
+    default to the 4096-angle stages (256-thread CTAs, several per SM), from
+    2^24 up to the large-array plans; the other operations' defaults do not
+    depend on the size."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k != "SINCOS_TUNE_CACHE"}
+    r = subprocess.run([sys.executable, "-c", _DEFAULTS.format(root=root)], capture_output=True,
+                       text=True, timeout=300, cwd=root, env=env)
+    assert r.returncode == 0, r.stdout + r.stderr
+    line = [ln for ln in r.stdout.splitlines() if ln.startswith("PLANS ")][0]
+    plans = {k: tuple(v) for k, v in json.loads(line[6:]).items()}
+    large = {"f32": (512, 2, 1, 0), "bf16": (512, 2, 3, 0), "f16": (512, 2, 3, 0)}
+    for key, p in plans.items():
+        op, dt, n = key.split()
+        n = int(n)
+        if op == "pairs":
+            assert p == ((256, 2, 2, 0) if n < 1 << 24 else large[dt]), key
+        elif op == "expi":
+            assert p == (512, 2, 1, 0), key
+        elif op == "backward":
+            assert p == (512, 2, 2, 16), key
+        else:
+            assert p == ((512, 2, 2, 0) if dt == "f32" else (1024, 2, 1, 16)), key
