@@ -391,6 +391,28 @@ def time_flushed(torch, fn, steps: int, warmup: int, flush) -> list:
     return per
 
 
+def time_each(torch, fn, steps: int, warmup: int, dist: Dist) -> list:
+    """Device ms of each of K calls of fn, timed one at a time with CUDA events
+    (a synchronize after each), the ranks' maxima per step.  For calls whose
+    duration varies from call to call by host-side effects (the driver's
+    staging of pageable copies), whose median is then the representative
+    figure."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    dist.barrier()
+    per = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        per.append(dist.max(a.elapsed_time(b)))
+    return per
+
+
 def gpu_local_cpus(torch, dev: int) -> set:
     """CPUs the kernel lists as local to the GPU's PCI function
     (local_cpulist in sysfs), among those this process may run on; empty if
@@ -877,23 +899,28 @@ def run_ours(args, dist: Dist):
             # without page-locked buffers gets (zero-copy where the device
             # reaches pageable memory), and the copy pipeline on it for context
             # (outputs written once by the CPU first: a page the GPU touches
-            # first is populated by that call, about 0.65 s for 2 GiB)
+            # first is populated by that call, about 0.65 s for 2 GiB).  Each
+            # call is timed alone and the median reported: the driver's
+            # staging of pageable copies makes some pipeline calls 4-18 times
+            # slower than the rest (74-322 ms against 18 ms).
             xp = torch.from_numpy(x_np)
             sp, cp = torch.empty(n, dtype=torch.float32), torch.empty(n, dtype=torch.float32)
             sp.fill_(0.0)
             cp.fill_(0.0)
-            for key, policy, p_steps in (("pageable", "auto", 5), ("pageable_pipeline", "pipeline", 3)):
+            for key, policy, p_steps in (("pageable", "auto", 5), ("pageable_pipeline", "pipeline", 7)):
                 api.sincos_host_route_set(policy)
                 try:
-                    tp, _, _ = time_loop(torch, lambda: api.sincos_pairs_host(xp, sp, cp, ws),
-                                         p_steps, 2, dist)
+                    per = time_each(torch, lambda: api.sincos_pairs_host(xp, sp, cp, ws),
+                                    p_steps, 2, dist)
                     route_p = api.sincos_host_last_path()
                 finally:
                     api.sincos_host_route_set("auto")
-                tp = dist.max(tp)
-                e2e[key] = {"value": (n_total if args.split else dist.world * n) * p_steps /
-                                     (tp * 1e-3),
-                            "unit": UNIT, "ms_per_step": tp / p_steps, "path": route_p}
+                tp = statistics.median(per)
+                e2e[key] = {"value": (n_total if args.split else dist.world * n) / (tp * 1e-3),
+                            "unit": UNIT, "ms_per_step": tp, "ms_min": min(per),
+                            "ms_max": max(per), "steps": p_steps,
+                            "timing": "median of calls timed one at a time",
+                            "path": route_p}
             assert torch.equal(sp[:1024], s[:1024].cpu()), "pageable path differs from device path"
             del xp, sp, cp
         del ws

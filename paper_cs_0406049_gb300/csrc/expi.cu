@@ -107,8 +107,12 @@ k_expi_bulk(const float *x, float *z, int64_t n, int64_t head, int64_t nchunks)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // The first stage's angles into L2 while the previous kernel drains, as
+    // in the single-array forward kernel.
+    if (tid == 0 && blockIdx.x < nchunks)
+        bulk_prefetch_l2(xg + blockIdx.x * (int64_t)kBulkChunk, kBulkChunk * 4);
     __syncthreads();
-    pdl_acquire();                 // no global access before the previous kernel is done
+    pdl_acquire();                 // no other global access before the previous kernel is done
     if (tid == 0) {
         for (int st = 0; st < kBulkStages; ++st) {
             const int64_t ch = blockIdx.x + (int64_t)st * gridDim.x;
