@@ -635,12 +635,23 @@ def extras(torch, api, workloads, dist, steps_hint: int, autotune: bool) -> dict
         api.sincos_autotune_pairs(xt, s, c)
     per = time_flushed(torch, lambda: api.sincos_pairs(xt, s, c), max(30, k // 4), 3, flush)
     ms = statistics.median(per)
+    # floors taken the same way: a one-element torch kernel, and torch's x * 2
+    # into s (4 MB read, 4 MB written).  The event timestamps of these short
+    # calls come in steps of about 2 us on GB300, so the medians do too.
+    tiny = torch.zeros(1, device="cuda")
+    floor_empty = statistics.median(time_flushed(torch, lambda: tiny.add_(1.0), max(30, k // 4), 3,
+                                                 flush))
+    floor_mul = statistics.median(time_flushed(torch, lambda: torch.mul(xt, 2.0, out=s),
+                                               max(30, k // 4), 3, flush))
+    del tiny
     api.sincos_pairs(xt, s, c)
     torch.cuda.synchronize()
     s_np, c_np = s.cpu().numpy(), c.cpu().numpy()
     out["plain_2p20"] = {
         "pairs_per_s": x.size / (ms * 1e-3), "us_per_call": 1e3 * ms,
         "l2_flushed": True, "bound": "launch and ramp (12.6 MB: about 2 us of HBM time)",
+        "floor_us": {"empty_one_element_kernel": 1e3 * floor_empty,
+                     "torch_mul_4MB_in_4MB_out": 1e3 * floor_mul},
         "errors": fp64_errors(x, s_np.astype(np.float64), c_np.astype(np.float64)),
         "accuracy": e1_stats(x, s_np, c_np),
         "accuracy_paper": {"rms_euclid": 1.2e-7, "max_euclid": 4.8e-7, "max_amplitude": 1.8e-7,
