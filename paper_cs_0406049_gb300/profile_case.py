@@ -26,6 +26,9 @@ def main(argv=None):
     p.add_argument("--launches", type=int, default=3)
     p.add_argument("--plan", default="",
                    help="block,unroll,ctas_per_sm,vec_bytes to use instead of the default plan")
+    p.add_argument("--reduction", choices=["plain", "compensated"], default=None,
+                   help="reduction of the forward ops (default: compensated for "
+                        "forward_compensated, else plain)")
     a = p.parse_args(argv)
     build.build()
     n = 1 << a.log2n
@@ -39,7 +42,7 @@ def main(argv=None):
     x = (torch.rand(n, device="cuda", generator=g) * 2000.0 - 1000.0).contiguous()
     if a.op.startswith("forward"):
         dt = torch.bfloat16 if a.op == "forward_bf16" else torch.float32
-        red = "compensated" if a.op == "forward_compensated" else "plain"
+        red = a.reduction or ("compensated" if a.op == "forward_compensated" else "plain")
         s = torch.empty(n, dtype=dt, device="cuda")
         c = torch.empty_like(s)
         use_plan("pairs", dt, n)
