@@ -3,7 +3,8 @@
 #include <atomic>
 #include <mutex>
 #include <string>
-#include <unordered_map>
+#include <map>
+#include <tuple>
 
 #include "bulk.cuh"
 #include "seg_check.h"
@@ -22,8 +23,12 @@ std::mutex g_dev_mu;
 DeviceInfo g_devices[kMaxDevices];
 bool g_dev_ready[kMaxDevices] = {false};
 
+// Resident CTAs per SM of a kernel at a block size on a device, with no
+// dynamic shared memory (kind 0) or with the bulk kernels' fixed amount
+// (kind 1).
+using OccKey = std::tuple<const void *, int, int, int>;   // kernel, block, device, kind
 std::mutex g_occ_mu;
-std::unordered_map<uint64_t, int> g_occ;   // (kernel, block, device) -> resident CTAs per SM
+std::map<OccKey, int> g_occ;
 
 }  // namespace
 
@@ -89,7 +94,7 @@ int resident_ctas(const void *kernel, int block, int want)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    const uint64_t key = ((uint64_t)(uintptr_t)kernel << 16) ^ ((uint64_t)block << 6) ^ (uint64_t)dev;
+    const OccKey key(kernel, block, dev, 0);
     int per_sm = -1;
     {
         std::lock_guard<std::mutex> lock(g_occ_mu);
@@ -117,8 +122,7 @@ int bulk_resident_ctas(const void *kernel, int block, size_t smem)
     thread_local size_t last_smem = 0;
     if (kernel == last_kernel && block == last_block && dev == last_dev && smem == last_smem)
         return last_ctas;
-    const uint64_t key = ((uint64_t)(uintptr_t)kernel << 16) ^ ((uint64_t)block << 6) ^
-                         (uint64_t)dev ^ 0x5bd1e995ull;
+    const OccKey key(kernel, block, dev, 1);
     {
         std::lock_guard<std::mutex> lock(g_occ_mu);
         auto it = g_occ.find(key);
