@@ -2,9 +2,10 @@
 // a JSON file) and the autotuner that fills it.
 //
 // A plan is (threads per CTA, vectors in flight per thread, resident CTAs per
-// SM, bytes per vector access -- or 0 for the bulk-copy path).  Plans are keyed by device ("<name>:<SMs>"), operation,
-// output dtype and the bit length of the element count, so one tuning run
-// per size class covers every later call in that class.
+// SM, bytes per vector access -- or 0 for the bulk-copy path).  Plans are
+// keyed by device ("<name>:<SMs>"), operation, output dtype and the bit
+// length of the element count, so one tuning run per size class covers every
+// later call in that class.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
