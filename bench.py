@@ -137,7 +137,8 @@ class Dist:
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "clocks.mem")
     REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_id: str):
@@ -157,7 +158,7 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             parts = [t.strip() for t in line.split(",")]
-            if len(parts) >= 8:
+            if len(parts) >= 9:
                 self.samples.append((time.time(), parts))
 
     def stop(self):
@@ -185,8 +186,30 @@ class ClockSampler:
         pw = [num(p[2]) for p in win]
         reasons = sorted({name for p in win for name, v in zip(self.REASONS, p[4:8])
                           if v.strip().lower() == "active"})
+        mem = [num(p[8]) for p in win]
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": reasons,
-                "samples": len(win), "power_w_max": max(pw)}
+                "samples": len(win), "power_w_max": max(pw), "mem_mhz": statistics.median(mem)}
+
+
+def live_copy_gbs(torch) -> float:
+    """This GPU's copy bandwidth now: torch's copy of 2^30 bf16 elements
+    (read + write bytes), best of ten, CUDA events; the same measurement as
+    the copy peak the roofline is quoted against, taken on this machine for
+    context."""
+    a = torch.empty(1 << 30, dtype=torch.bfloat16, device="cuda")
+    b = torch.empty_like(a)
+    best = float("inf")
+    for i in range(12):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        if i >= 2:
+            best = min(best, e0.elapsed_time(e1))
+    nbytes = 2 * a.numel() * a.element_size()
+    del a, b
+    return nbytes / (best * 1e-3) / 1e9
 
 
 def gpu_query_id(torch) -> str:
@@ -875,6 +898,8 @@ def run_ours(args, dist: Dist):
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_PAIR * n / (kernel_ms * 1e-3) / 1e9
     traffic = profiled_traffic()
+    # the same copy measurement as the peak, on this machine now (boxes differ)
+    live_copy = live_copy_gbs(torch)
 
     rng = np.random.default_rng(0)
     idx = rng.integers(0, n, 1 << 20)
@@ -978,6 +1003,7 @@ def run_ours(args, dist: Dist):
                                     f"k_forward<float, plain, normalized, {plan['unroll']}, "
                                     f"{plan['vec_bytes']}>"),
                          "bytes_per_launch": BYTES_PER_PAIR * n, "kernel_ms": kernel_ms,
+                         "peak_live_copy": live_copy, "frac_of_live_copy": achieved / live_copy,
                          **vendor_peak(torch, achieved)},
             "errors_vs_fp64": err,
             "paper_context": PAPER_CONTEXT,
