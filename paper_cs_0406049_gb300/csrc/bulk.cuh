@@ -176,14 +176,17 @@ __device__ __forceinline__ void bulk_tile_vec(const float *xi, OutT *so, OutT *c
         in[q + 3] = v.w;
     }
     float sv[E], cv[E];
-    // Packed (the single-array kernel's binary32 tiles, normalized set): two
-    // angles per packed FP32 instruction (core_x2.cuh, the same bits), which
-    // shortens the compute phase between stages (+0.4 % plain, +1.1 %
-    // compensated at 2^28).  For 16-bit outputs the packed form needs more
-    // registers than three CTAs of 512 threads can share and loses (6066
+    // Packed (the single-array kernel's binary32 tiles): two angles per
+    // packed FP32 instruction (core_x2.cuh, the same bits), which shortens
+    // the compute phase between stages (+0.4 % plain, +1.1 % compensated at
+    // 2^28 with the normalized set; with the dagger set +0.3-1.3 % on the
+    // one-CTA plan, +10-14 % on 128-thread CTAs, within 0.5 % on the
+    // 512-thread small-stage plan).  For 16-bit outputs the packed form needs
+    // more registers than three CTAs of 512 threads can share and loses (6066
     // against 6532 GB/s); the batched ring kernel uses it with the compensated
-    // reduction only (+1.2 % there, -0.5 % with the plain one).
-    if constexpr (PACK && COEF == COEF_NORMALIZED && sizeof(OutT) == 4) {
+    // reduction only (+1.2 % there with the normalized set, +6 % with the
+    // dagger set; -0.5 % with the plain reduction).
+    if constexpr (PACK && sizeof(OutT) == 4) {
 #pragma unroll
         for (int i = 0; i < E; i += 2) {
             float2 s2, c2;

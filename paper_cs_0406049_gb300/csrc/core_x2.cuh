@@ -14,8 +14,9 @@
 // The packed instructions take no negated operands, so the steps whose
 // operands carry a sign (the differences of squares and the final products)
 // run as scalar instructions, where the sign is free.
-// Used by the Huygens kernel (bound by the FMA pipe) and by the bulk forward
-// kernel's binary32 tiles (shorter compute phase between memory stages).
+// Used by the Huygens kernel (bound by the FMA pipe) and by the bulk
+// kernels' binary32 tiles, with either coefficient set (shorter compute phase
+// between memory stages).
 #pragma once
 
 #include "core.cuh"
@@ -36,11 +37,10 @@ __device__ __forceinline__ float2 reduce_x2(float2 x)
     return __fadd2_rn(q, make_float2(rintf(-q.x), rintf(-q.y)));    // q - rint(q)
 }
 
-// Two pairs with the normalized coefficient set.
+// Two pairs, either coefficient set.
 template <int RED, int COEF>
 __device__ __forceinline__ void pair_x2(float2 x, float2 &s, float2 &c)
 {
-    static_assert(COEF == COEF_NORMALIZED, "pair_x2 implements the normalized set");
     using S = Series<COEF>;
     const float2 q1 = reduce_x2<RED>(x);
     const float2 q2 = __fmul2_rn(q1, q1);
@@ -57,16 +57,30 @@ __device__ __forceinline__ void pair_x2(float2 x, float2 &s, float2 &c)
     const float2 c1c1 = __fmul2_rn(c1, c1);
     const float2 c2 = make_float2(__fmaf_rn(-s1.x, s1.x, c1c1.x), __fmaf_rn(-s1.y, s1.y, c1c1.y));
     const float2 s2 = __fmul2_rn(splat2(2.0f), __fmul2_rn(s1, c1));
-    // Drift factor fma(-s2, s2, fma(-c2, c2, 2)), computed as its negation
-    // nfix = fma(s2, s2, fma(c2, c2, -2)); neither fma can cancel to zero,
-    // since c2^2 and s2^2 are at most about 1.
-    const float2 nfix = __ffma2_rn(s2, s2, __ffma2_rn(c2, c2, splat2(-2.0f)));
-    // Eq. (1), second doubling, then the correction (times -nfix = fix).
     const float2 c2c2 = __fmul2_rn(c2, c2);
-    const float2 c3 = make_float2(__fmaf_rn(-s2.x, s2.x, c2c2.x), __fmaf_rn(-s2.y, s2.y, c2c2.y));
-    const float2 s3 = __fmul2_rn(splat2(2.0f), __fmul2_rn(s2, c2));
-    c = make_float2(__fmul_rn(c3.x, -nfix.x), __fmul_rn(c3.y, -nfix.y));
-    s = make_float2(__fmul_rn(s3.x, -nfix.x), __fmul_rn(s3.y, -nfix.y));
+    if constexpr (COEF == COEF_DAGGER) {
+        // Drift factor 1/fma(s2, s2, c2^2): the sum on the packed pipe, the
+        // IEEE reciprocals scalar; then the second doubling and the
+        // correction, the products with fix packed (no sign to move).
+        const float2 d = __ffma2_rn(s2, s2, c2c2);
+        const float2 fix = make_float2(__frcp_rn(d.x), __frcp_rn(d.y));
+        const float2 c3 =
+            make_float2(__fmaf_rn(-s2.x, s2.x, c2c2.x), __fmaf_rn(-s2.y, s2.y, c2c2.y));
+        const float2 s3 = __fmul2_rn(splat2(2.0f), __fmul2_rn(s2, c2));
+        c = __fmul2_rn(c3, fix);
+        s = __fmul2_rn(s3, fix);
+    } else {
+        // Drift factor fma(-s2, s2, fma(-c2, c2, 2)), computed as its
+        // negation nfix = fma(s2, s2, fma(c2, c2, -2)); neither fma can cancel
+        // to zero, since c2^2 and s2^2 are at most about 1.
+        const float2 nfix = __ffma2_rn(s2, s2, __ffma2_rn(c2, c2, splat2(-2.0f)));
+        // Eq. (1), second doubling, then the correction (times -nfix = fix).
+        const float2 c3 =
+            make_float2(__fmaf_rn(-s2.x, s2.x, c2c2.x), __fmaf_rn(-s2.y, s2.y, c2c2.y));
+        const float2 s3 = __fmul2_rn(splat2(2.0f), __fmul2_rn(s2, c2));
+        c = make_float2(__fmul_rn(c3.x, -nfix.x), __fmul_rn(c3.y, -nfix.y));
+        s = make_float2(__fmul_rn(s3.x, -nfix.x), __fmul_rn(s3.y, -nfix.y));
+    }
 }
 
 }  // namespace sincos_gb300

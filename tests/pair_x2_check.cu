@@ -18,7 +18,7 @@ __device__ __forceinline__ bool same(float a, float b)
     return (a != a && b != b) || __float_as_uint(a) == __float_as_uint(b);
 }
 
-template <int RED>
+template <int RED, int COEF>
 __global__ void k_check(unsigned long long *mismatches, unsigned *first_bad)
 {
     const uint64_t npairs = 1ull << 31;
@@ -27,10 +27,10 @@ __global__ void k_check(unsigned long long *mismatches, unsigned *first_bad)
         const float x0 = __uint_as_float((unsigned)(2 * k));
         const float x1 = __uint_as_float((unsigned)(2 * k + 1));
         float s0, c0, s1, c1;
-        pair<RED, COEF_NORMALIZED>(x0, s0, c0);
-        pair<RED, COEF_NORMALIZED>(x1, s1, c1);
+        pair<RED, COEF>(x0, s0, c0);
+        pair<RED, COEF>(x1, s1, c1);
         float2 s, c;
-        pair_x2<RED, COEF_NORMALIZED>(make_float2(x0, x1), s, c);
+        pair_x2<RED, COEF>(make_float2(x0, x1), s, c);
         const bool ok0 = same(s.x, s0) && same(c.x, c0);
         const bool ok1 = same(s.y, s1) && same(c.y, c1);
         if (!ok0 || !ok1) {
@@ -42,10 +42,11 @@ __global__ void k_check(unsigned long long *mismatches, unsigned *first_bad)
 
 }  // namespace
 
-// Runs the check for one reduction (0 plain, 1 compensated); returns 0 and
-// the mismatch count and the smallest mismatching bit pattern (0xffffffff if
-// none), or a CUDA error code.
-extern "C" int pair_x2_check(int red, unsigned long long *mismatches_out, unsigned *first_bad_out)
+// Runs the check for one reduction (0 plain, 1 compensated) and coefficient
+// set (0 normalized, 1 dagger); returns 0 and the mismatch count and the
+// smallest mismatching bit pattern (0xffffffff if none), or a CUDA error code.
+extern "C" int pair_x2_check(int red, int coef, unsigned long long *mismatches_out,
+                             unsigned *first_bad_out)
 {
     unsigned long long *d_mis = nullptr;
     unsigned *d_first = nullptr;
@@ -57,10 +58,14 @@ extern "C" int pair_x2_check(int red, unsigned long long *mismatches_out, unsign
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
-        if (red == 1)
-            k_check<RED_COMPENSATED><<<sms * 8, 256>>>(d_mis, d_first);
+        if (red == 1 && coef == 1)
+            k_check<RED_COMPENSATED, COEF_DAGGER><<<sms * 8, 256>>>(d_mis, d_first);
+        else if (red == 1)
+            k_check<RED_COMPENSATED, COEF_NORMALIZED><<<sms * 8, 256>>>(d_mis, d_first);
+        else if (coef == 1)
+            k_check<RED_PLAIN, COEF_DAGGER><<<sms * 8, 256>>>(d_mis, d_first);
         else
-            k_check<RED_PLAIN><<<sms * 8, 256>>>(d_mis, d_first);
+            k_check<RED_PLAIN, COEF_NORMALIZED><<<sms * 8, 256>>>(d_mis, d_first);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
